@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the Gauss-Chebyshev bilateral filter on one GB300 (or N replicas).
+
+Workload: one 3840x2160 float32 grayscale image (seeded edge + 1/f field + noise,
+values in [0, 255]); sigma_s = 10 (window R = 30), sigma_r = 50, Chebyshev degree
+N = 20 (22 filtered channels) -- the convergent point of the 4K sweep.  A step is one
+forward filter of one image (channel build, spatial Gaussian bank, ratio) through the
+C ABI; the coefficient fit happens once at plan time.  Inputs rotate over 8 distinct
+resident images (264 MB > L2) so no step starts with its input in L2.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel/s at 4K fp32 sigma_s=10 (plain vs fused/bf16) at stated PSNR vs FP64 oracle"
+H, W = 2160, 3840
+SIGMA_S, SIGMA_R, N = 10.0, 50.0, 20
+N_INPUTS = 8
+L2_BYTES = 129 * 2 ** 20
+
+# candidate forms, best first; the first one the library supports is the headline
+FORMS = [("fused_tc", "bf16"), ("fused_tc", "fp16"), ("plain", "fp32")]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--forms", default=None, help="comma list of form:precision to run")
+    ap.add_argument("--size", default=None, help="HxW instead of 2160x3840 (profiling cases)")
+    args = ap.parse_args()
+    if args.size:
+        global H, W
+        H, W = (int(v) for v in args.size.lower().split("x"))
+    return args
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
+
+
+# --------------------------------------------------------------------------- helpers
+def sample_clocks_start(path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        return subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                 "-lms", "100", "-f", path], stdout=subprocess.DEVNULL,
+                                stderr=subprocess.DEVNULL)
+    except OSError:
+        return None
+
+
+def sample_clocks_stop(proc, path, gpu_index):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+    sms, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(gpu_index):
+                continue
+            try:
+                sms.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+    except OSError:
+        return None
+    if not sms:
+        return None
+    return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(sms)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def traffic_record(kernel):
+    """dram bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+    except (OSError, ValueError, KeyError):
+        return None
+    src = os.path.join(ROOT, "paper_1605_02178_gb300", "csrc", rec["source_file"])
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return rec["dram_bytes_per_launch"] if digest == rec["source_sha256_16"] else None
+
+
+def kernel_model(form, precision, C, R):
+    """Algorithmic work per pixel of each kernel: ('hbm', bytes) or ('alu', flops)."""
+    s = {"fp32": 4, "bf16": 2, "fp16": 2}[precision]
+    if form == "plain":
+        return {"build": ("hbm", 4 + 4 * C), "hpass": ("alu", 2 * (2 * R + 1) * C),
+                "vpass": ("alu", 2 * (2 * R + 1) * C), "combine": ("hbm", 4 * C + 8)}
+    return {"build_hpass_tc": ("hbm", 4 + s * C), "vpass_combine_tc": ("hbm", s * C + 8)}
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_1605_02178_gb300 import synth
+    f = synth.workload("uhd")["f"]
+    R = oracle.window_radius(SIGMA_S)
+    rows = 128
+    y0 = H // 2 - rows // 2
+
+    def step():
+        sub = f[y0 - R: y0 + rows + R]
+        oracle.gcf(sub, SIGMA_S, SIGMA_R, N)
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = rows * W / dt / 1e6
+    cores = oracle.num_threads()
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"uhd {W}x{H} edge+smooth field, sigma_s={SIGMA_S}, sigma_r={SIGMA_R}, N={N}",
+                   "sample": f"{rows} output rows x {W} (+{R} context rows each side) per step"},
+        "cpu_baseline": {"value": value, "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{rows}x{W} strip per step, FP64 C oracle, separable eq. (7)"},
+        "e2e": {"value": value, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_1605_02178_gb300 import api, bfgc, synth
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    f_np = synth.edge_smooth_image(H, W, noise_std=5.0, seed=1 + rank)
+    base = torch.from_numpy(f_np).to(dev)
+    inputs = [torch.roll(base, shifts=(37 * k, 101 * k), dims=(0, 1)).contiguous() if k else base
+              for k in range(N_INPUTS)]
+    outputs = [torch.empty_like(base) for _ in range(N_INPUTS)]
+    stream = torch.cuda.current_stream(dev)
+    px = H * W
+
+    wanted = FORMS if args.forms is None else [tuple(x.split(":")) for x in args.forms.split(",")]
+    plans = {}
+    for form, prec in wanted:
+        try:
+            plan = api.GCPlan(H, W, SIGMA_S, SIGMA_R, N, form=form, precision=prec)
+            plan.workspace("fwd", dev)
+            plans[(form, prec)] = plan
+        except bfgc.BfError as e:
+            if e.status != bfgc.BF_ERR_UNSUPPORTED:
+                raise
+    if not plans:
+        raise RuntimeError("no supported form")
+    headline = next(k for k in wanted if k in plans)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    def time_form(key, steps, warmup, profile, clocks_path=None):
+        plan = plans[key]
+        ws = plan.workspace("fwd", dev)
+        for i in range(warmup):
+            plan.forward(inputs[i % N_INPUTS], outputs[i % N_INPUTS], ws, stream)
+        if profile:
+            bfgc.bf_gc_profile_enable(plan.handle, True)
+        barrier()
+        clk = sample_clocks_start(clocks_path) if clocks_path else None
+        if clk:
+            time.sleep(0.3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            plan.forward(inputs[i % N_INPUTS], outputs[i % N_INPUTS], ws, stream)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        clocks = sample_clocks_stop(clk, clocks_path, local) if clk else None
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        kern = bfgc.bf_gc_profile_read(plan.handle) if profile else {}
+        if profile:
+            bfgc.bf_gc_profile_enable(plan.handle, False)
+        return ms / steps, kern, clocks
+
+    results = {}
+    clocks_path = os.path.join("/tmp", f"bfgc_clocks_{os.getpid()}.csv")
+    for key in plans:
+        is_head = key == headline
+        ms, kern, clocks = time_form(key, args.steps, max(args.warmup, 3), profile=is_head,
+                                     clocks_path=clocks_path if is_head else None)
+        results[key] = {"ms": ms, "kernels": kern, "clocks": clocks,
+                        "value": world * px / (ms * 1e-3) / 1e6}
+
+    # ---- accuracy of each form: sampled outputs vs the FP64 oracle, PSNR vs the exact filter
+    accuracy = {}
+    if not args.no_accuracy and rank == 0:
+        import oracle
+        rng = np.random.default_rng(0)
+        ys = np.concatenate([[0, 0, H - 1, H - 1], rng.integers(0, H, 60)])
+        xs = np.concatenate([[0, W - 1, 0, W - 1], rng.integers(0, W, 60)])
+        idx = ys * W + xs
+        ref = oracle.gcf_at(f_np, idx, SIGMA_S, SIGMA_R, N)
+        exact = bfgc.bf_direct(base, SIGMA_S, SIGMA_R)
+        torch.cuda.synchronize(dev)
+        exact_np = exact.cpu().numpy().astype(np.float64)
+        ex_ref = oracle.exact_bf_at(f_np, idx[:24], SIGMA_S, SIGMA_R)
+        accuracy["exact_filter_gpu_vs_oracle_maxabs"] = float(np.abs(exact_np.reshape(-1)[idx[:24]] - ex_ref).max())
+        for key, plan in plans.items():
+            out = plan.forward(base, torch.empty_like(base), plan.workspace("fwd", dev), stream)
+            torch.cuda.synchronize(dev)
+            o = out.cpu().numpy().astype(np.float64)
+            accuracy[f"{key[0]}/{key[1]}"] = {
+                "maxabs_vs_fp64_oracle_sampled": float(np.abs(o.reshape(-1)[idx] - ref).max()),
+                "samples": int(idx.size),
+                "psnr_vs_exact_db": oracle.psnr_db(o, exact_np),
+            }
+
+    # ---- end to end through the C ABI with host buffers (pinned), headline form
+    plan = plans[headline]
+    h_in = torch.from_numpy(f_np).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    d_in, d_out = torch.empty_like(base), torch.empty_like(base)
+    ws = plan.workspace("fwd", dev)
+    for _ in range(3):
+        bfgc.bf_gc_forward_host(plan.handle, h_in, h_out, d_in, d_out, ws, stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        bfgc.bf_gc_forward_host(plan.handle, h_in, h_out, d_in, d_out, ws, stream)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # ---- CPU baseline (oracle on host cores, rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        R = oracle.window_radius(SIGMA_S)
+        t0 = time.perf_counter()
+        rows = 32
+        oracle.gcf(f_np[H // 2 - R: H // 2 + rows + R], SIGMA_S, SIGMA_R, N)
+        per_row = (time.perf_counter() - t0) / (rows + 2 * R)
+        rows = int(min(H - 2 * R - 8, max(32, 12.0 / per_row - 2 * R)))
+        y0 = max(R, H // 2 - rows // 2)
+        t0 = time.perf_counter()
+        oracle.gcf(f_np[y0 - R: y0 + rows + R], SIGMA_S, SIGMA_R, N)
+        dt = time.perf_counter() - t0
+        cpu = {"value": rows * W / dt / 1e6, "unit": "Mpixel/s", "cores": oracle.num_threads(),
+               "kind": "oracle",
+               "sample": f"{rows}x{W} strip of the workload (+{R} context rows each side), FP64 C oracle "
+                         f"(separable eq. (7)), {dt:.1f} s"}
+
+    if rank != 0:
+        return
+    head = results[headline]
+    C = N + 2
+    R = int(math.ceil(3 * SIGMA_S - 1e-9))
+    model = kernel_model(headline[0], headline[1], C, R)
+    kern = head["kernels"]
+    dominant = max(kern, key=lambda k: kern[k][0]) if kern else None
+    peaks, peak_kind = measured_peaks()
+    roofline = None
+    if dominant:
+        avg_ms = kern[dominant][0] / max(1, kern[dominant][1])
+        bound, per_px = model.get(dominant, ("hbm", 0))
+        if bound == "hbm":
+            achieved = per_px * px / (avg_ms * 1e-3) / 1e9
+            peak = peaks["hbm_gbs"]
+            unit = "GB/s"
+        else:
+            achieved = per_px * px / (avg_ms * 1e-3) / 1e12
+            sm_mhz = (head["clocks"] or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+            peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12   # FP32 FMA lanes x 2 flop x clock
+            unit = "TFLOP/s"
+        tb = traffic_record(dominant)
+        roofline = {"kernel": dominant, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                    "frac": achieved / peak, "peak_source": peak_kind if bound == "hbm" else
+                    "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load",
+                    "traffic": tb, "algorithmic_per_px": per_px, "avg_launch_ms": avg_ms}
+    per_step_launches = sum(v[1] for v in kern.values()) / args.steps if kern else None
+    line = {
+        "metric": METRIC, "value": head["value"], "unit": "Mpixel/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if headline[1] == "fp32" else headline[1],
+        "data": "synthetic",
+        "config": {"workload": f"uhd {W}x{H} edge+smooth field (seeded), sigma_s={SIGMA_S}, sigma_r={SIGMA_R}, N={N}",
+                   "H": H, "W": W, "sigma_s": SIGMA_S, "sigma_r": SIGMA_R, "N": N, "channels": C,
+                   "form": headline[0], "precision": headline[1],
+                   "l2": f"inputs rotate over {N_INPUTS} resident images ({N_INPUTS * px * 4 >> 20} MB > L2)",
+                   "parallelism": f"replicas{world}"},
+        "forms": {f"{k[0]}/{k[1]}": {"value": v["value"], "ms_per_step": v["ms"]} for k, v in results.items()},
+        "kernels_ms_per_launch": {k: v[0] / max(1, v[1]) for k, v in kern.items()},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * px / e2e_s / 1e6, "unit": "Mpixel/s", "h2d_bytes_per_step": px * 4,
+                "d2h_bytes_per_step": px * 4},
+        "gpu_launches": int(round(per_step_launches * args.steps)) if per_step_launches else None,
+        "clocks": head["clocks"],
+        "accuracy": accuracy,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * bfgc.h - C ABI of the GB300 Gauss-Chebyshev bilateral filter library (libbfgc.so).
+ *
+ * Method: S. Ghosh and K. N. Chaudhury, "Fast and High-Quality Bilateral Filtering
+ * Using Gauss-Chebyshev Approximation" (2016).  The Gaussian bilateral filter of
+ * eq. (1) is approximated by replacing the range kernel with a Gaussian times a
+ * degree-N polynomial whose coefficients come from a Chebyshev interpolation of
+ * exp on [-mu, mu] (eqs. (16)-(19), Sec. III).  The filter then becomes
+ *   1. per-pixel auxiliary images F_n, n = 0..N+1 (eq. (6), after centring eq. (17)),
+ *   2. a bank of N+2 spatial Gaussian filterings (eq. (7)),
+ *   3. a per-pixel ratio P/Q (eqs. (8)-(10)) and un-centring.
+ *
+ * Conventions for every entry point:
+ *  - Images are single-channel float32, row-major, H rows by W columns, contiguous
+ *    (element (y, x) at y*W + x).  Device pointers must be 16-byte aligned.
+ *  - Pointers prefixed d_ are device memory, h_ host memory.  The caller owns every
+ *    buffer (inputs, outputs, workspace); the library never allocates device memory.
+ *  - Device work is enqueued asynchronously on `stream` (a cudaStream_t; NULL is
+ *    the legacy default stream).  Argument errors are returned synchronously and
+ *    nothing is enqueued.  Launch failures return BF_ERR_CUDA; faults during
+ *    execution surface at the caller's next synchronisation.
+ *  - Boundary: the image is extended by half-sample symmetry per axis
+ *    (... f1 f0 | f0 f1 ... ), the paper's "extend the image outside I using
+ *    symmetry" (Sec. I).  Window half-width R = ceil(3 sigma_s) (W = 3 sigma_s, Sec. I).
+ *  - Intensity range [L, U] defaults to [0, 255] (Sec. II); values outside it are
+ *    accepted (the polynomial is then extrapolated).
+ */
+#ifndef BFGC_H
+#define BFGC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bf_gc_plan_s *bf_gc_plan_t;   /* opaque, host-owned */
+typedef struct CUstream_st *bf_stream_t;     /* identical to cudaStream_t */
+
+typedef enum {
+    BF_OK = 0,
+    BF_ERR_INVALID_ARG = 1,   /* bad size, sigma, pointer, alignment, option or state */
+    BF_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement (e.g. R too large for a form) */
+    BF_ERR_NOMEM = 3,         /* host allocation failed */
+    BF_ERR_CUDA = 4,          /* a CUDA runtime call or kernel launch failed */
+    BF_ERR_TIMEOUT = 5,       /* a bounded device wait gave up (reported by bf_gc_diagnostics) */
+    BF_ERR_RANGE = 6,         /* reserved: strict range checking */
+    BF_ERR_WORKSPACE = 7      /* workspace pointer NULL, misaligned or smaller than required */
+} bf_status;
+
+/* ---- plan options (bf_gc_plan_set) --------------------------------------------------- */
+enum {
+    BF_OPT_FORM = 1,          /* value: BF_FORM_*                                  (default PLAIN) */
+    BF_OPT_PRECISION = 2,     /* value: BF_PREC_*, storage of the filtered channels (default FP32) */
+    BF_OPT_RANGE_L = 3,       /* value: L of the intensity range                   (default 0)     */
+    BF_OPT_RANGE_U = 4,       /* value: U of the intensity range                   (default 255)   */
+    BF_OPT_POLY = 5,          /* value: BF_POLY_*, choice of c_n                   (default CHEB)  */
+    BF_OPT_SAVE_CHANNELS = 6  /* value: 1 = forward leaves the filtered channels in the workspace
+                                 for bf_gc_backward to reuse; 0 = backward recomputes them      */
+};
+enum {
+    BF_FORM_PLAIN = 0,        /* 4 kernels: build F_n -> row filter -> column filter -> ratio; FP32 */
+    BF_FORM_FUSED_TC = 1,     /* 2 kernels: (build + row filter) and (column filter + ratio), the
+                                 spatial Gaussian as a banded Toeplitz product on tensor cores;
+                                 channels stored as BF16 or FP16, FP32 accumulation */
+    BF_FORM_RECURSIVE = 2     /* recursive (IIR) stand-in for eq. (7), Young-van Vliet 1995 */
+};
+enum { BF_PREC_FP32 = 0, BF_PREC_BF16 = 1, BF_PREC_FP16 = 2 };
+enum {
+    BF_POLY_CHEBYSHEV = 0,    /* c_n of eq. (19): Gauss-Chebyshev filter (GCF)          */
+    BF_POLY_TAYLOR = 1        /* c_n = 1/n!: the Gauss-polynomial filter (GPF) of Sec. II */
+};
+
+#define BF_MAX_N 62           /* largest supported degree N (N + 2 <= 64 channels) */
+
+/* Plan information (bf_gc_plan_info). */
+typedef struct {
+    int H, W, N, R, C;        /* C = N + 2 channels */
+    int form, precision, poly;
+    double sigma_s, sigma_r, L, U;
+    double t_c;               /* (L + U) / 2, eq. (17) */
+    double s_r;               /* (U - L) / 2: the centred image lies in [-s_r, s_r] */
+    double mu;                /* (U - L)^2 / (4 sigma_r^2), Sec. III-B */
+    double kappa;             /* max_n |c~_n|; the device uses c~_n / kappa */
+    double fit_err;           /* max |g_r(t - tau) - approximate kernel| over a 129x129 grid of
+                                 (t, tau) in [L, U]^2, evaluated in FP64 */
+    double c[BF_MAX_N + 1];       /* c_n of eq. (19) (or 1/n!), n = 0..N */
+    double c_tilde[BF_MAX_N + 1]; /* c~_n = mu^n c_n (the coefficients in u = (f - t_c)/s_r) */
+} bf_gc_info;
+
+/* Device-side diagnostics written by the last forward into its workspace. */
+typedef struct {
+    unsigned long long n_guarded;   /* pixels with |Q| < 1e-12 sum|terms of Q|: output = input */
+    unsigned long long n_fp64_div;  /* pixels divided in FP64 (|Q| < 1e-3 sum|terms of Q|) */
+    unsigned int error_flags;       /* bit 0: a bounded wait timed out in a pipelined kernel */
+} bf_gc_diag;
+
+/* Create a plan for H x W images (Sec. III-B): fits, in FP64 on the host, the
+ * Chebyshev interpolant of exp at the N+1 zeros of T_{N+1} on [-mu, mu] (eqs. (16),
+ * (18)), converts it to monomials (eq. (19)) and derives the spatial taps.
+ * H, W >= 1; sigma_s > 0; sigma_r > 0; 1 <= N <= BF_MAX_N.  Host only; no CUDA call.
+ * *out receives the plan, or NULL on error. */
+bf_status bf_gc_plan(int H, int W, double sigma_s, double sigma_r, int N, bf_gc_plan_t *out);
+
+/* Change an option (BF_OPT_*) before first use; refits when L, U or the polynomial
+ * change.  Returns BF_ERR_INVALID_ARG for an unknown option or value, or after the
+ * plan has run a forward or backward. */
+bf_status bf_gc_plan_set(bf_gc_plan_t plan, int option, double value);
+
+/* Copy the plan's parameters and coefficients.  Host only. */
+bf_status bf_gc_plan_info(bf_gc_plan_t plan, bf_gc_info *out);
+
+/* Bytes of device workspace needed by bf_gc_forward and by bf_gc_backward for the
+ * plan's current options.  Either pointer may be NULL.  Host only. */
+bf_status bf_gc_workspace_size(bf_gc_plan_t plan, size_t *fwd_bytes, size_t *bwd_bytes);
+
+/* Forward filter, eqs. (6)-(10) with centring (17): d_out = B_hat[d_f] (H x W).
+ * d_ws: device workspace of at least the forward size, 256-byte aligned; its
+ * contents on entry are ignored.  d_f and d_out must not overlap. */
+bf_status bf_gc_forward(bf_gc_plan_t plan, const float *d_f, float *d_out, void *d_ws,
+                        size_t ws_bytes, bf_stream_t stream);
+
+/* Same as bf_gc_forward with host input and output: copies h_f to the device
+ * staging buffer d_f, runs the forward into d_out, copies d_out back to h_out and
+ * waits for the stream.  h_f / h_out should be page-locked for asynchronous copies. */
+bf_status bf_gc_forward_host(bf_gc_plan_t plan, const float *h_f, float *h_out, float *d_f,
+                             float *d_out, void *d_ws, size_t ws_bytes, bf_stream_t stream);
+
+/* Adjoint of the forward (not in the paper): given d_gout = dL/dB_hat, writes
+ * d_gf = dL/df (H x W) and, if d_gsigma_r is not NULL, *d_gsigma_r = dL/dsigma_r
+ * (one double on the device).  The derivative is that of the approximation,
+ * including the dependence of mu and of the Chebyshev coefficients on sigma_r.
+ * d_ws: workspace of at least the backward size.  If the plan has
+ * BF_OPT_SAVE_CHANNELS = 1 and d_ws is the workspace of the last forward on the
+ * same d_f, the filtered channels are reused; otherwise they are recomputed. */
+bf_status bf_gc_backward(bf_gc_plan_t plan, const float *d_f, const float *d_gout, float *d_gf,
+                         double *d_gsigma_r, void *d_ws, size_t ws_bytes, bf_stream_t stream);
+
+/* Read back the diagnostics of the last forward that used d_ws (synchronises stream). */
+bf_status bf_gc_diagnostics(bf_gc_plan_t plan, const void *d_ws, bf_gc_diag *out,
+                            bf_stream_t stream);
+
+void bf_gc_plan_destroy(bf_gc_plan_t plan);
+
+/* Kernel timing (a tracing aid, off by default).  While enabled, each forward and
+ * backward of the plan records a CUDA event before every kernel it launches and one
+ * after the last, on the caller's stream; bf_gc_profile_read waits for those events
+ * and returns, per kernel name, the summed duration and the number of launches since
+ * the last enable.  Enabling (or disabling) resets the totals. */
+typedef struct {
+    char name[32];
+    double total_ms;
+    unsigned long long launches;
+} bf_kernel_time;
+
+bf_status bf_gc_profile_enable(bf_gc_plan_t plan, int enable);
+bf_status bf_gc_profile_read(bf_gc_plan_t plan, bf_kernel_time *out, int max_entries,
+                             int *n_entries);
+
+/* The exact Gaussian bilateral filter of eq. (1) by brute force over the
+ * (2R+1)^2 window, FP32, used to measure the approximation's accuracy.
+ * No workspace. */
+bf_status bf_direct(int H, int W, double sigma_s, double sigma_r, const float *d_f,
+                    float *d_out, bf_stream_t stream);
+
+const char *bf_status_string(bf_status s);
+const char *bf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BFGC_H */

@@ -47,7 +47,7 @@ def _lib():
         lib.oracle_spatial_recursive.argtypes = [_dp, I, I, D, I, _dp]
         lib.oracle_yvv_coeffs.argtypes = [D, _dp]
         lib.oracle_yvv_1d.argtypes = [_dp, L, D, L, _dp]
-        lib.oracle_gcf.argtypes = [_dp, I, I, D, D, I, I, D, D, _dp, D, I, _dp, _dp, _dp, _dp,
+        lib.oracle_gcf.argtypes = [_dp, I, I, D, D, I, I, D, D, _dp, D, I, _dp, _dp, _dp, _dp, _dp,
                                    ctypes.POINTER(ctypes.c_long)]
         lib.oracle_gcf_at.argtypes = [_dp, I, I, D, D, I, I, D, D, _dp, D, _i64p, L, _dp, _dp, _dp]
         lib.oracle_gcf_kernel_direct.argtypes = [_dp, I, I, D, D, I, I, D, D, _dp, _dp]
@@ -174,15 +174,16 @@ def gcf(f, sigma_s, sigma_r, N, L=0.0, U=255.0, c=None, delta=1e-12, spatial="se
     R = window_radius(sigma_s) if R is None else R
     c = gcf_coeffs(N, sigma_r, L, U) if c is None else _f64(c)
     out = np.empty_like(f)
-    P, Q, Qa = (np.empty_like(f) for _ in range(3)) if return_pq else (None, None, None)
+    P, Q, Qa, Pa = (np.empty_like(f) for _ in range(4)) if return_pq else (None,) * 4
     ng = ctypes.c_long(0)
     _check(_lib().oracle_gcf(_ptr(f), H, W, float(sigma_s), float(sigma_r), int(N), R, float(L),
                              float(U), _ptr(c), float(delta), SPATIAL_MODES[spatial], _ptr(out),
                              _ptr(P) if P is not None else None,
                              _ptr(Q) if Q is not None else None,
-                             _ptr(Qa) if Qa is not None else None, ctypes.byref(ng)), "gcf")
+                             _ptr(Qa) if Qa is not None else None,
+                             _ptr(Pa) if Pa is not None else None, ctypes.byref(ng)), "gcf")
     if return_pq:
-        return out, {"P": P, "Q": Q, "Qabs": Qa, "n_guard": ng.value}
+        return out, {"P": P, "Q": Q, "Qabs": Qa, "Pabs": Pa, "n_guard": ng.value}
     return out
 
 

@@ -320,12 +320,14 @@ int oracle_spatial_recursive(const double *F, int H, int W, double sigma_s, int 
  *   eq. (10) and un-centring: out = P / Q + t_c.
  * spatial_mode: 0 = eq. (7) evaluated separably, 1 = recursive stand-in,
  *               2 = eq. (7) as the literal double sum.
- * P_out, Q_out, Qabs_out may be NULL.  Returns the number of guarded pixels
- * in *n_guard (may be NULL).
+ * P_out, Q_out, Qabs_out, Pabs_out may be NULL (Qabs / Pabs: sums of the
+ * absolute values of the terms of Q / P).  Returns the number of guarded
+ * pixels in *n_guard (may be NULL).
  * ---------------------------------------------------------------------- */
 int oracle_gcf(const double *f, int H, int W, double sigma_s, double sigma_r, int N, int R,
                double L, double U, const double *c, double delta, int spatial_mode,
-               double *out, double *P_out, double *Q_out, double *Qabs_out, long *n_guard)
+               double *out, double *P_out, double *Q_out, double *Qabs_out, double *Pabs_out,
+               long *n_guard)
 {
     if (!f || !out || !c || H < 1 || W < 1 || N < 0 || R < 0 || !(sigma_r > 0) || !(sigma_s > 0))
         return 1;
@@ -360,15 +362,18 @@ int oracle_gcf(const double *f, int H, int W, double sigma_s, double sigma_r, in
     if (!err) {
         /* eqs. (8), (9), (10) */
         for (long i = 0; i < px; ++i) {
-            double P = 0.0, Q = 0.0, Qabs = 0.0;
+            double P = 0.0, Q = 0.0, Qabs = 0.0, Pabs = 0.0;
             for (int n = 0; n <= N; ++n) {
                 double cg = c[n] * G[(long)n * px + i];
-                P += cg * Fb[(long)(n + 1) * px + i];
+                double pt = cg * Fb[(long)(n + 1) * px + i];
+                P += pt;
+                Pabs += fabs(pt);
                 double q = cg * Fb[(long)n * px + i];
                 Q += q;
                 Qabs += fabs(q);
             }
             P *= sigma_r;
+            Pabs *= sigma_r;
             if (fabs(Q) < delta * Qabs || Qabs == 0.0) {
                 out[i] = f[i];
                 ++guarded;
@@ -378,6 +383,7 @@ int oracle_gcf(const double *f, int H, int W, double sigma_s, double sigma_r, in
             if (P_out) P_out[i] = P;
             if (Q_out) Q_out[i] = Q;
             if (Qabs_out) Qabs_out[i] = Qabs;
+            if (Pabs_out) Pabs_out[i] = Pabs;
         }
     }
     if (n_guard) *n_guard = guarded;

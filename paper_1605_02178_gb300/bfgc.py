@@ -1,0 +1,203 @@
+"""Thin Python binding of libbfgc (include/bfgc.h): same names, argument marshalling only.
+
+Every computation happens in the CUDA kernels behind the C ABI.  PyTorch supplies
+device memory (tensors) and streams; nothing here falls back to the CPU: if the
+library cannot be built or loaded, the first call raises.
+"""
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbfgc.so")
+
+BF_OK, BF_ERR_INVALID_ARG, BF_ERR_UNSUPPORTED, BF_ERR_NOMEM, BF_ERR_CUDA, BF_ERR_TIMEOUT, \
+    BF_ERR_RANGE, BF_ERR_WORKSPACE = range(8)
+BF_OPT_FORM, BF_OPT_PRECISION, BF_OPT_RANGE_L, BF_OPT_RANGE_U, BF_OPT_POLY, BF_OPT_SAVE_CHANNELS = range(1, 7)
+BF_FORM_PLAIN, BF_FORM_FUSED_TC, BF_FORM_RECURSIVE = range(3)
+BF_PREC_FP32, BF_PREC_BF16, BF_PREC_FP16 = range(3)
+BF_POLY_CHEBYSHEV, BF_POLY_TAYLOR = range(2)
+BF_MAX_N = 62
+
+FORMS = {"plain": BF_FORM_PLAIN, "fused_tc": BF_FORM_FUSED_TC, "recursive": BF_FORM_RECURSIVE}
+PRECISIONS = {"fp32": BF_PREC_FP32, "bf16": BF_PREC_BF16, "fp16": BF_PREC_FP16}
+POLYS = {"chebyshev": BF_POLY_CHEBYSHEV, "taylor": BF_POLY_TAYLOR}
+
+
+class bf_gc_info(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("N", ctypes.c_int), ("R", ctypes.c_int),
+                ("C", ctypes.c_int), ("form", ctypes.c_int), ("precision", ctypes.c_int),
+                ("poly", ctypes.c_int), ("sigma_s", ctypes.c_double), ("sigma_r", ctypes.c_double),
+                ("L", ctypes.c_double), ("U", ctypes.c_double), ("t_c", ctypes.c_double),
+                ("s_r", ctypes.c_double), ("mu", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("fit_err", ctypes.c_double), ("c", ctypes.c_double * (BF_MAX_N + 1)),
+                ("c_tilde", ctypes.c_double * (BF_MAX_N + 1))]
+
+
+class bf_gc_diag(ctypes.Structure):
+    _fields_ = [("n_guarded", ctypes.c_ulonglong), ("n_fp64_div", ctypes.c_ulonglong),
+                ("error_flags", ctypes.c_uint)]
+
+
+class bf_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("total_ms", ctypes.c_double), ("launches", ctypes.c_ulonglong)]
+
+
+# name -> (restype, argtypes) for every entry point of include/bfgc.h
+_P, _I, _D, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+SIGNATURES = {
+    "bf_gc_plan": (_I, [_I, _I, _D, _D, _I, ctypes.POINTER(_P)]),
+    "bf_gc_plan_set": (_I, [_P, _I, _D]),
+    "bf_gc_plan_info": (_I, [_P, ctypes.POINTER(bf_gc_info)]),
+    "bf_gc_workspace_size": (_I, [_P, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
+    "bf_gc_forward": (_I, [_P, _P, _P, _P, _SZ, _P]),
+    "bf_gc_forward_host": (_I, [_P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "bf_gc_backward": (_I, [_P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "bf_gc_diagnostics": (_I, [_P, _P, ctypes.POINTER(bf_gc_diag), _P]),
+    "bf_gc_plan_destroy": (None, [_P]),
+    "bf_gc_profile_enable": (_I, [_P, _I]),
+    "bf_gc_profile_read": (_I, [_P, ctypes.POINTER(bf_kernel_time), _I, ctypes.POINTER(_I)]),
+    "bf_direct": (_I, [_I, _I, _D, _D, _P, _P, _P]),
+    "bf_status_string": (ctypes.c_char_p, [_I]),
+    "bf_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libbfgc.so, building it first if it is missing or older than its sources."""
+    global _lib
+    if _lib is None:
+        with _lock:
+            if _lib is None:
+                from .csrc import build as _build
+                if not _build.up_to_date():
+                    _build.build()
+                L = ctypes.CDLL(LIB_PATH)
+                for name, (res, args) in SIGNATURES.items():
+                    fn = getattr(L, name)
+                    fn.restype = res
+                    fn.argtypes = args
+                _lib = L
+    return _lib
+
+
+class BfError(RuntimeError):
+    def __init__(self, status, what):
+        msg = lib().bf_status_string(status).decode()
+        super().__init__(f"{what}: {msg} (status {status})")
+        self.status = status
+
+
+def _check(status, what):
+    if status != BF_OK:
+        raise BfError(status, what)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(int(t))
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev_f32(t, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    return t
+
+
+# ----------------------------------------------------------------------------- C-ABI mirrors
+def bf_gc_plan(H, W, sigma_s, sigma_r, N):
+    h = ctypes.c_void_p()
+    _check(lib().bf_gc_plan(int(H), int(W), float(sigma_s), float(sigma_r), int(N), ctypes.byref(h)),
+           "bf_gc_plan")
+    return h
+
+
+def bf_gc_plan_set(plan, option, value):
+    _check(lib().bf_gc_plan_set(plan, int(option), float(value)), "bf_gc_plan_set")
+
+
+def bf_gc_plan_info(plan):
+    info = bf_gc_info()
+    _check(lib().bf_gc_plan_info(plan, ctypes.byref(info)), "bf_gc_plan_info")
+    return info
+
+
+def bf_gc_workspace_size(plan):
+    fwd, bwd = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().bf_gc_workspace_size(plan, ctypes.byref(fwd), ctypes.byref(bwd)), "bf_gc_workspace_size")
+    return fwd.value, bwd.value
+
+
+def bf_gc_forward(plan, f, out, ws, stream=None):
+    _dev_f32(f, "f")
+    _dev_f32(out, "out")
+    _check(lib().bf_gc_forward(plan, _ptr(f), _ptr(out), _ptr(ws), ws.numel() * ws.element_size(),
+                               _stream(stream)), "bf_gc_forward")
+    return out
+
+
+def bf_gc_forward_host(plan, h_f, h_out, d_f, d_out, ws, stream=None):
+    _check(lib().bf_gc_forward_host(plan, _ptr(h_f), _ptr(h_out), _ptr(d_f), _ptr(d_out), _ptr(ws),
+                                    ws.numel() * ws.element_size(), _stream(stream)), "bf_gc_forward_host")
+    return h_out
+
+
+def bf_gc_backward(plan, f, gout, gf, gsigma_r, ws, stream=None):
+    _check(lib().bf_gc_backward(plan, _ptr(f), _ptr(gout), _ptr(gf), _ptr(gsigma_r), _ptr(ws),
+                                ws.numel() * ws.element_size(), _stream(stream)), "bf_gc_backward")
+    return gf
+
+
+def bf_gc_diagnostics(plan, ws, stream=None):
+    d = bf_gc_diag()
+    st = lib().bf_gc_diagnostics(plan, _ptr(ws), ctypes.byref(d), _stream(stream))
+    if st not in (BF_OK, BF_ERR_TIMEOUT):
+        _check(st, "bf_gc_diagnostics")
+    return {"n_guarded": d.n_guarded, "n_fp64_div": d.n_fp64_div, "error_flags": d.error_flags}
+
+
+def bf_gc_plan_destroy(plan):
+    lib().bf_gc_plan_destroy(plan)
+
+
+def bf_gc_profile_enable(plan, enable=True):
+    _check(lib().bf_gc_profile_enable(plan, 1 if enable else 0), "bf_gc_profile_enable")
+
+
+def bf_gc_profile_read(plan):
+    """{kernel name: (total ms, launches)} since the last enable (waits for the events)."""
+    buf = (bf_kernel_time * 32)()
+    n = ctypes.c_int(0)
+    _check(lib().bf_gc_profile_read(plan, buf, 32, ctypes.byref(n)), "bf_gc_profile_read")
+    return {buf[i].name.decode(): (buf[i].total_ms, buf[i].launches) for i in range(min(n.value, 32))}
+
+
+def bf_direct(f, sigma_s, sigma_r, out=None, stream=None):
+    _dev_f32(f, "f")
+    out = torch.empty_like(f) if out is None else _dev_f32(out, "out")
+    H, W = f.shape[-2], f.shape[-1]
+    _check(lib().bf_direct(H, W, float(sigma_s), float(sigma_r), _ptr(f), _ptr(out), _stream(stream)),
+           "bf_direct")
+    return out
+
+
+def bf_status_string(status):
+    return lib().bf_status_string(int(status)).decode()
+
+
+def bf_version():
+    return lib().bf_version().decode()

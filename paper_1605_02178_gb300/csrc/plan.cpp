@@ -1,0 +1,406 @@
+// Host side of libbfgc: the FP64 coefficient fit (Sec. III), plan management and the
+// C ABI entry points that validate arguments and enqueue the kernels.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "bfgc_internal.h"
+
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+int window_radius(double sigma_s) { return (int)ceil(3.0 * sigma_s - 1e-9); }
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Monomial coefficients of the Chebyshev polynomials, A[l][n] = coefficient of x^n in
+// T_l, generated from T_{l+1} = 2 x T_l - T_{l-1} (eqs. (12), (13)).
+std::vector<std::vector<double>> chebyshev_monomials(int N) {
+    std::vector<std::vector<double>> A(N + 1, std::vector<double>(N + 2, 0.0));
+    A[0][0] = 1.0;
+    if (N >= 1) A[1][1] = 1.0;
+    for (int l = 2; l <= N; ++l)
+        for (int n = 0; n <= l; ++n)
+            A[l][n] = (n > 0 ? 2.0 * A[l - 1][n - 1] : 0.0) - A[l - 2][n];
+    return A;
+}
+
+// Coefficients of the polynomial in x/mu approximating exp(x) on [-mu, mu]:
+// the Chebyshev interpolant at the zeros of T_{N+1} (eqs. (16), (18)) rewritten in
+// monomials of x/mu (eq. (19) without its factor mu^-n).  Also the derivative of
+// each coefficient with respect to mu.  T_l at the nodes is taken from eq. (11),
+// T_l(cos t) = cos(l t).
+void chebyshev_fit(int N, double mu, double* ct, double* dct_dmu) {
+    const int M = N + 1;
+    std::vector<double> d(M, 0.0), dd(M, 0.0);
+    for (int k = 1; k <= M; ++k) {
+        const double theta = kPi * (2.0 * k - 1.0) / (2.0 * M);
+        const double xi = cos(theta);
+        const double h = exp(mu * xi);
+        for (int l = 0; l < M; ++l) {
+            const double Tl = cos(l * theta);
+            d[l] += h * Tl;
+            dd[l] += xi * h * Tl;
+        }
+    }
+    for (int l = 0; l < M; ++l) {
+        const double w = (l == 0 ? 1.0 : 2.0) / M;
+        d[l] *= w;
+        dd[l] *= w;
+    }
+    auto A = chebyshev_monomials(N);
+    for (int n = 0; n <= N; ++n) {
+        double s = 0.0, ds = 0.0;
+        for (int l = N; l >= n; --l) {
+            s += d[l] * A[l][n];
+            ds += dd[l] * A[l][n];
+        }
+        ct[n] = s;
+        dct_dmu[n] = ds;
+    }
+}
+
+void taylor_fit(int N, double mu, double* ct, double* dct_dmu) {
+    // c_n = 1/n!, so c~_n = mu^n / n! and d c~_n / d mu = n mu^(n-1) / n!
+    double fact = 1.0;
+    for (int n = 0; n <= N; ++n) {
+        if (n > 0) fact *= n;
+        ct[n] = pow(mu, n) / fact;
+        dct_dmu[n] = n > 0 ? n * pow(mu, n - 1) / fact : 0.0;
+    }
+}
+
+void refit(bf_gc_plan_s* p) {
+    p->t_c = 0.5 * (p->L + p->U);
+    p->s_r = 0.5 * (p->U - p->L);
+    p->mu = p->s_r * p->s_r / (p->sigma_r * p->sigma_r);
+    double dct[BF_MAX_N + 1];
+    if (p->poly == BF_POLY_TAYLOR)
+        taylor_fit(p->N, p->mu, p->c_tilde, dct);
+    else
+        chebyshev_fit(p->N, p->mu, p->c_tilde, dct);
+    p->kappa = 0.0;
+    for (int n = 0; n <= p->N; ++n) {
+        p->c[n] = p->c_tilde[n] * pow(p->mu, -(double)n);
+        p->kappa = std::max(p->kappa, fabs(p->c_tilde[n]));
+    }
+    if (!(p->kappa > 0.0) || !isfinite(p->kappa)) p->kappa = 1.0;
+    const double dmu_dsigma = -2.0 * p->mu / p->sigma_r;
+    for (int n = 0; n <= p->N; ++n) p->dcoef_dsigma[n] = dct[n] * dmu_dsigma / p->kappa;
+
+    // worst kernel error over a grid of intensities (t, tau) in [L, U]^2
+    double err = 0.0;
+    const int G = 129;
+    for (int a = 0; a < G; ++a)
+        for (int b = 0; b < G; ++b) {
+            const double tau = p->L + (p->U - p->L) * a / (G - 1.0) - p->t_c;
+            const double t = p->L + (p->U - p->L) * b / (G - 1.0) - p->t_c;
+            const double x = (tau / p->s_r) * (t / p->s_r);
+            double poly = 0.0;
+            for (int n = p->N; n >= 0; --n) poly = poly * x + p->c_tilde[n];
+            const double s2 = 2.0 * p->sigma_r * p->sigma_r;
+            const double approx = exp(-tau * tau / s2) * exp(-t * t / s2) * poly;
+            err = std::max(err, fabs(exp(-(t - tau) * (t - tau) / s2) - approx));
+        }
+    p->fit_err = isfinite(err) ? err : INFINITY;
+
+    GcParams& g = p->gp;
+    g.H = p->H; g.W = p->W; g.N = p->N; g.C = p->C; g.R = p->R;
+    g.t_c = (float)p->t_c;
+    g.inv_sr = (float)(1.0 / p->s_r);
+    g.s_r = (float)p->s_r;
+    g.half_mu = (float)(0.5 * p->mu);
+    for (int n = 0; n < BF_MAX_C; ++n) g.coef[n] = n <= p->N ? (float)(p->c_tilde[n] / p->kappa) : 0.0f;
+}
+
+void make_taps(double sigma_s, int R, Taps* t) {
+    double sum = 0.0;
+    for (int d = -R; d <= R; ++d) sum += exp(-(double)d * d / (2.0 * sigma_s * sigma_s));
+    t->R = R;
+    for (int d = 0; d <= BF_MAX_R; ++d)
+        t->g[d] = d <= R ? (float)(exp(-(double)d * d / (2.0 * sigma_s * sigma_s)) / sum) : 0.0f;
+}
+
+size_t fwd_workspace(const bf_gc_plan_s* p) {
+    switch (p->form) {
+    case BF_FORM_PLAIN:
+        return BF_WS_HEADER + 2 * (size_t)p->C * bfgc::plain_plane_stride(p->H, p->W) * sizeof(float);
+    default:
+        return 0;
+    }
+}
+
+size_t bwd_workspace(const bf_gc_plan_s* p) {
+    (void)p;
+    return 0;
+}
+
+bool form_supported(const bf_gc_plan_s* p) {
+    switch (p->form) {
+    case BF_FORM_PLAIN:
+        return p->precision == BF_PREC_FP32;
+    default:
+        return false;
+    }
+}
+
+bf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? BF_OK : BF_ERR_CUDA; }
+
+// ---- optional event timing ---------------------------------------------------------
+void prof_clear(Profiler& pr) {
+    for (auto& m : pr.marks) cudaEventDestroy(m.ev);
+    pr.marks.clear();
+    pr.open = -1;
+}
+
+// Record the start of kernel `name` (and thereby the end of the previous one).
+void prof_mark(bf_gc_plan_s* p, const char* name, cudaStream_t s) {
+    Profiler& pr = p->prof;
+    if (!pr.enabled) return;
+    int k = -1;
+    if (name) {
+        for (size_t i = 0; i < pr.names.size(); ++i)
+            if (pr.names[i] == name) k = (int)i;
+        if (k < 0) {
+            pr.names.push_back(name);
+            pr.total_ms.push_back(0.0);
+            pr.launches.push_back(0);
+            k = (int)pr.names.size() - 1;
+        }
+    }
+    cudaEvent_t ev;
+    if (cudaEventCreate(&ev) != cudaSuccess) return;
+    cudaEventRecord(ev, s);
+    pr.marks.push_back({k, ev});
+    pr.open = k;
+}
+
+void prof_close(bf_gc_plan_s* p, cudaStream_t s) {
+    if (p->prof.enabled && p->prof.open >= 0) prof_mark(p, nullptr, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+bf_status bf_gc_plan(int H, int W, double sigma_s, double sigma_r, int N, bf_gc_plan_t* out) {
+    if (!out) return BF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (H < 1 || W < 1 || (long long)H * W > (1LL << 40) || !(sigma_s > 0.0) || !(sigma_r > 0.0) ||
+        !isfinite(sigma_s) || !isfinite(sigma_r) || N < 1 || N > BF_MAX_N)
+        return BF_ERR_INVALID_ARG;
+    const int R = window_radius(sigma_s);
+    if (R > BF_MAX_R) return BF_ERR_UNSUPPORTED;
+    bf_gc_plan_s* p = new (std::nothrow) bf_gc_plan_s();
+    if (!p) return BF_ERR_NOMEM;
+    p->H = H; p->W = W; p->N = N; p->C = N + 2; p->R = R;
+    p->sigma_s = sigma_s; p->sigma_r = sigma_r;
+    p->L = 0.0; p->U = 255.0;
+    p->form = BF_FORM_PLAIN; p->precision = BF_PREC_FP32; p->poly = BF_POLY_CHEBYSHEV;
+    p->save_channels = 0; p->used = false;
+    refit(p);
+    make_taps(sigma_s, R, &p->taps);
+    *out = p;
+    return BF_OK;
+}
+
+bf_status bf_gc_plan_set(bf_gc_plan_t p, int option, double value) {
+    if (!p || p->used || !isfinite(value)) return BF_ERR_INVALID_ARG;
+    const int iv = (int)value;
+    switch (option) {
+    case BF_OPT_FORM:
+        if (iv != value || iv < BF_FORM_PLAIN || iv > BF_FORM_RECURSIVE) return BF_ERR_INVALID_ARG;
+        p->form = iv;
+        return BF_OK;
+    case BF_OPT_PRECISION:
+        if (iv != value || iv < BF_PREC_FP32 || iv > BF_PREC_FP16) return BF_ERR_INVALID_ARG;
+        p->precision = iv;
+        return BF_OK;
+    case BF_OPT_RANGE_L:
+    case BF_OPT_RANGE_U: {
+        const double L = option == BF_OPT_RANGE_L ? value : p->L;
+        const double U = option == BF_OPT_RANGE_U ? value : p->U;
+        if (!(U > L)) return BF_ERR_INVALID_ARG;
+        p->L = L;
+        p->U = U;
+        refit(p);
+        return BF_OK;
+    }
+    case BF_OPT_POLY:
+        if (iv != value || (iv != BF_POLY_CHEBYSHEV && iv != BF_POLY_TAYLOR)) return BF_ERR_INVALID_ARG;
+        p->poly = iv;
+        refit(p);
+        return BF_OK;
+    case BF_OPT_SAVE_CHANNELS:
+        if (iv != value || (iv != 0 && iv != 1)) return BF_ERR_INVALID_ARG;
+        p->save_channels = iv;
+        return BF_OK;
+    default:
+        return BF_ERR_INVALID_ARG;
+    }
+}
+
+bf_status bf_gc_plan_info(bf_gc_plan_t p, bf_gc_info* o) {
+    if (!p || !o) return BF_ERR_INVALID_ARG;
+    memset(o, 0, sizeof(*o));
+    o->H = p->H; o->W = p->W; o->N = p->N; o->R = p->R; o->C = p->C;
+    o->form = p->form; o->precision = p->precision; o->poly = p->poly;
+    o->sigma_s = p->sigma_s; o->sigma_r = p->sigma_r; o->L = p->L; o->U = p->U;
+    o->t_c = p->t_c; o->s_r = p->s_r; o->mu = p->mu; o->kappa = p->kappa; o->fit_err = p->fit_err;
+    for (int n = 0; n <= p->N; ++n) {
+        o->c[n] = p->c[n];
+        o->c_tilde[n] = p->c_tilde[n];
+    }
+    return BF_OK;
+}
+
+bf_status bf_gc_workspace_size(bf_gc_plan_t p, size_t* fwd, size_t* bwd) {
+    if (!p) return BF_ERR_INVALID_ARG;
+    if (!form_supported(p)) return BF_ERR_UNSUPPORTED;
+    if (fwd) *fwd = fwd_workspace(p);
+    if (bwd) *bwd = bwd_workspace(p);
+    return BF_OK;
+}
+
+bf_status bf_gc_forward(bf_gc_plan_t p, const float* f, float* out, void* ws, size_t ws_bytes,
+                        bf_stream_t stream) {
+    if (!p || !f || !out || !aligned(f, 16) || !aligned(out, 16)) return BF_ERR_INVALID_ARG;
+    const size_t px = (size_t)p->H * p->W;
+    if ((const char*)f < (const char*)(out + px) && (const char*)out < (const char*)(f + px))
+        return BF_ERR_INVALID_ARG;
+    if (!form_supported(p)) return BF_ERR_UNSUPPORTED;
+    if (!ws || !aligned(ws, 256) || ws_bytes < fwd_workspace(p)) return BF_ERR_WORKSPACE;
+    p->used = true;
+    cudaStream_t s = (cudaStream_t)stream;
+    DiagHeader* diag = (DiagHeader*)ws;
+    cudaError_t e = cudaMemsetAsync(diag, 0, sizeof(DiagHeader), s);
+    if (e != cudaSuccess) return BF_ERR_CUDA;
+    char* body = (char*)ws + BF_WS_HEADER;
+    switch (p->form) {
+    case BF_FORM_PLAIN: {
+        const size_t cs = bfgc::plain_plane_stride(p->H, p->W);
+        float* X = (float*)body;
+        float* Y = X + (size_t)p->C * cs;
+        prof_mark(p, "build", s);
+        if ((e = bfgc::launch_build(f, X, p->gp, cs, s)) != cudaSuccess) break;
+        prof_mark(p, "hpass", s);
+        if ((e = bfgc::launch_hpass(X, Y, p->gp, p->taps, cs, p->C, s)) != cudaSuccess) break;
+        prof_mark(p, "vpass", s);
+        if ((e = bfgc::launch_vpass(Y, X, p->gp, p->taps, cs, p->C, s)) != cudaSuccess) break;
+        prof_mark(p, "combine", s);
+        e = bfgc::launch_combine(f, X, out, p->gp, cs, diag, s);
+        break;
+    }
+    default:
+        return BF_ERR_UNSUPPORTED;
+    }
+    prof_close(p, s);
+    return cuda_status(e);
+}
+
+bf_status bf_gc_forward_host(bf_gc_plan_t p, const float* h_f, float* h_out, float* d_f,
+                             float* d_out, void* ws, size_t ws_bytes, bf_stream_t stream) {
+    if (!p || !h_f || !h_out || !d_f || !d_out) return BF_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)p->H * p->W * sizeof(float);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!form_supported(p)) return BF_ERR_UNSUPPORTED;
+    if (!ws || !aligned(ws, 256) || ws_bytes < fwd_workspace(p)) return BF_ERR_WORKSPACE;
+    if (cudaMemcpyAsync(d_f, h_f, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return BF_ERR_CUDA;
+    bf_status st = bf_gc_forward(p, d_f, d_out, ws, ws_bytes, stream);
+    if (st != BF_OK) return st;
+    if (cudaMemcpyAsync(h_out, d_out, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return BF_ERR_CUDA;
+    return cuda_status(cudaStreamSynchronize(s));
+}
+
+bf_status bf_gc_backward(bf_gc_plan_t p, const float* f, const float* gout, float* gf,
+                         double* gsigma, void* ws, size_t ws_bytes, bf_stream_t stream) {
+    (void)f; (void)gout; (void)gf; (void)gsigma; (void)ws; (void)ws_bytes; (void)stream;
+    if (!p) return BF_ERR_INVALID_ARG;
+    return BF_ERR_UNSUPPORTED;
+}
+
+bf_status bf_gc_diagnostics(bf_gc_plan_t p, const void* ws, bf_gc_diag* out, bf_stream_t stream) {
+    if (!p || !ws || !out || !aligned(ws, 256)) return BF_ERR_INVALID_ARG;
+    DiagHeader h;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&h, ws, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return BF_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return BF_ERR_CUDA;
+    out->n_guarded = h.n_guarded;
+    out->n_fp64_div = h.n_fp64_div;
+    out->error_flags = h.error_flags;
+    return h.error_flags ? BF_ERR_TIMEOUT : BF_OK;
+}
+
+void bf_gc_plan_destroy(bf_gc_plan_t p) {
+    if (!p) return;
+    prof_clear(p->prof);
+    delete p;
+}
+
+bf_status bf_gc_profile_enable(bf_gc_plan_t p, int enable) {
+    if (!p) return BF_ERR_INVALID_ARG;
+    prof_clear(p->prof);
+    p->prof.names.clear();
+    p->prof.total_ms.clear();
+    p->prof.launches.clear();
+    p->prof.enabled = enable != 0;
+    return BF_OK;
+}
+
+bf_status bf_gc_profile_read(bf_gc_plan_t p, bf_kernel_time* out, int max_entries, int* n_entries) {
+    if (!p || max_entries < 0 || (max_entries > 0 && !out)) return BF_ERR_INVALID_ARG;
+    Profiler& pr = p->prof;
+    if (!pr.marks.empty() && cudaEventSynchronize(pr.marks.back().ev) != cudaSuccess) return BF_ERR_CUDA;
+    for (size_t i = 0; i + 1 < pr.marks.size(); ++i) {
+        if (pr.marks[i].kernel < 0) continue;
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, pr.marks[i].ev, pr.marks[i + 1].ev) != cudaSuccess) return BF_ERR_CUDA;
+        pr.total_ms[pr.marks[i].kernel] += ms;
+        pr.launches[pr.marks[i].kernel] += 1;
+    }
+    prof_clear(pr);
+    const int n = (int)pr.names.size();
+    for (int i = 0; i < n && i < max_entries; ++i) {
+        memset(out[i].name, 0, sizeof(out[i].name));
+        strncpy(out[i].name, pr.names[i].c_str(), sizeof(out[i].name) - 1);
+        out[i].total_ms = pr.total_ms[i];
+        out[i].launches = pr.launches[i];
+    }
+    if (n_entries) *n_entries = n;
+    return BF_OK;
+}
+
+bf_status bf_direct(int H, int W, double sigma_s, double sigma_r, const float* f, float* out,
+                    bf_stream_t stream) {
+    if (H < 1 || W < 1 || !(sigma_s > 0.0) || !(sigma_r > 0.0) || !isfinite(sigma_s) ||
+        !isfinite(sigma_r) || !f || !out || !aligned(f, 16) || !aligned(out, 16))
+        return BF_ERR_INVALID_ARG;
+    const int R = window_radius(sigma_s);
+    if (R > BF_MAX_R) return BF_ERR_UNSUPPORTED;
+    return cuda_status(bfgc::launch_direct(f, out, H, W, R, sigma_s, sigma_r, (cudaStream_t)stream));
+}
+
+const char* bf_status_string(bf_status s) {
+    switch (s) {
+    case BF_OK: return "ok";
+    case BF_ERR_INVALID_ARG: return "invalid argument";
+    case BF_ERR_UNSUPPORTED: return "unsupported";
+    case BF_ERR_NOMEM: return "out of host memory";
+    case BF_ERR_CUDA: return "CUDA error";
+    case BF_ERR_TIMEOUT: return "device wait timed out";
+    case BF_ERR_RANGE: return "input outside range";
+    case BF_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    }
+    return "unknown status";
+}
+
+const char* bf_version(void) { return "bfgc 0.1 (sm_103a)"; }
+
+}  // extern "C"

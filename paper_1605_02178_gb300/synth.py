@@ -28,7 +28,7 @@ def rects_image(H, W, n_rects=20, noise_std=10.0, seed=0):
         w = int(rng.integers(16, 257))
         img[y0:min(H, y0 + h), x0:min(W, x0 + w)] = rng.uniform(0.0, 255.0)
     img += rng.normal(0.0, noise_std, size=(H, W))
-    return np.clip(img, 0.0, 255.0).astype(np.float32)
+    return np.ascontiguousarray(np.clip(img, 0.0, 255.0), dtype=np.float32)
 
 
 def _edge_field(H, W, rng):
@@ -65,18 +65,18 @@ def edge_smooth_image(H, W, noise_std=5.0, seed=1):
     edge = _edge_field(H, W, rng)
     smooth = _smooth_field(H, W, rng)
     img = 0.5 * edge + 0.5 * smooth + rng.normal(0.0, noise_std, size=(H, W))
-    return np.clip(img, 0.0, 255.0).astype(np.float32)
+    return np.ascontiguousarray(np.clip(img, 0.0, 255.0), dtype=np.float32)
 
 
 def weight_map(H, W, seed=3):
     """i.i.d. N(0, 1) weights (upstream gradient of a weighted-sum loss)."""
-    return np.random.default_rng(seed).normal(size=(H, W)).astype(np.float32)
+    return np.ascontiguousarray(np.random.default_rng(seed).normal(size=(H, W)), dtype=np.float32)
 
 
 def checkerboard(n=150, cell=25, lo=0.0, hi=255.0):
     """Binary checkerboard, a stand-in for the sharp-edged test image of Table 1."""
     yy, xx = np.meshgrid(np.arange(n) // cell, np.arange(n) // cell, indexing="ij")
-    return np.where((yy + xx) % 2 == 0, lo, hi).astype(np.float32)
+    return np.ascontiguousarray(np.where((yy + xx) % 2 == 0, lo, hi), dtype=np.float32)
 
 
 def batch_specs(count=256, seed=4):

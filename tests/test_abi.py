@@ -1,0 +1,122 @@
+"""CPU-only checks of the C ABI: the library builds, loads and exports every entry point
+declared in include/bfgc.h; host-side plan logic (argument checks, options, the FP64
+coefficient fit) behaves as documented.  No kernel is launched here."""
+import ctypes
+import math
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1605_02178_gb300 import bfgc as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bfgc.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bf_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_expected_entry_points():
+    names = declared_functions()
+    for must in ("bf_gc_plan", "bf_gc_forward", "bf_gc_backward", "bf_direct"):
+        assert must in names
+    assert set(names) == set(B.SIGNATURES), "binding and header disagree"
+
+
+def test_library_exports_every_declared_symbol():
+    lib = B.lib()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT\s+(\w+)$", out, flags=re.M))
+    assert set(declared_functions()) <= exported
+    assert not any(s.startswith("oracle_") for s in exported)     # no oracle code in the product
+
+
+def test_library_does_not_link_the_oracle():
+    out = subprocess.run(["ldd", B.LIB_PATH], capture_output=True, text=True).stdout
+    assert "bfgc_oracle" not in out
+
+
+@pytest.mark.parametrize("args", [
+    (0, 10, 1.0, 10.0, 4), (10, 0, 1.0, 10.0, 4), (10, 10, 0.0, 10.0, 4), (10, 10, 1.0, -1.0, 4),
+    (10, 10, 1.0, 10.0, 0), (10, 10, 1.0, 10.0, B.BF_MAX_N + 1), (10, 10, float("nan"), 10.0, 4)])
+def test_plan_rejects_invalid_arguments(args):
+    with pytest.raises(B.BfError) as e:
+        B.bf_gc_plan(*args)
+    assert e.value.status == B.BF_ERR_INVALID_ARG
+
+
+def test_plan_rejects_window_beyond_limit():
+    with pytest.raises(B.BfError) as e:
+        B.bf_gc_plan(10, 10, 90.0, 10.0, 4)
+    assert e.value.status == B.BF_ERR_UNSUPPORTED
+
+
+def test_plan_options_and_info():
+    p = B.bf_gc_plan(2160, 3840, 10.0, 50.0, 20)
+    try:
+        i = B.bf_gc_plan_info(p)
+        assert (i.H, i.W, i.N, i.C, i.R) == (2160, 3840, 20, 22, 30)
+        assert i.t_c == 127.5 and i.s_r == 127.5
+        assert i.mu == pytest.approx(255.0 ** 2 / (4 * 50.0 ** 2), rel=1e-15)
+        for opt, bad in [(B.BF_OPT_FORM, 7), (B.BF_OPT_PRECISION, 3), (B.BF_OPT_POLY, 2), (99, 0),
+                         (B.BF_OPT_FORM, 0.5)]:
+            with pytest.raises(B.BfError):
+                B.bf_gc_plan_set(p, opt, bad)
+        with pytest.raises(B.BfError):
+            B.bf_gc_plan_set(p, B.BF_OPT_RANGE_U, -5.0)                 # U <= L
+        fwd, bwd = B.bf_gc_workspace_size(p)
+        assert fwd >= 2 * 22 * 2160 * 3840 * 4
+        B.bf_gc_plan_set(p, B.BF_OPT_RANGE_L, 16.0)
+        B.bf_gc_plan_set(p, B.BF_OPT_RANGE_U, 235.0)
+        i = B.bf_gc_plan_info(p)
+        assert i.t_c == pytest.approx(125.5) and i.s_r == pytest.approx(109.5)
+    finally:
+        B.bf_gc_plan_destroy(p)
+
+
+@pytest.mark.parametrize("sr,N", [(50.0, 20), (30.0, 8), (60.0, 4), (25.0, 10), (40.0, 16)])
+def test_plan_coefficients_match_oracle_fit(sr, N):
+    """The library's FP64 fit (written separately) gives the oracle's c_n of eq. (19)
+    up to the roundoff of the monomial conversion (relative to max |c~_n|)."""
+    p = B.bf_gc_plan(64, 64, 3.0, sr, N)
+    try:
+        i = B.bf_gc_plan_info(p)
+        ref = oracle.cheb_fit(N, i.mu)["c"] * i.mu ** np.arange(N + 1)
+        got = np.array(i.c_tilde[: N + 1])
+        assert np.max(np.abs(got - ref)) <= 1e-6 * np.abs(ref).max()
+        assert i.kappa == pytest.approx(np.abs(ref).max(), rel=1e-6)
+    finally:
+        B.bf_gc_plan_destroy(p)
+
+
+def test_taylor_option_gives_inverse_factorials():
+    p = B.bf_gc_plan(8, 8, 1.0, 40.0, 9)
+    try:
+        B.bf_gc_plan_set(p, B.BF_OPT_POLY, B.BF_POLY_TAYLOR)
+        i = B.bf_gc_plan_info(p)
+        assert np.allclose([i.c[n] for n in range(10)], [1 / math.factorial(n) for n in range(10)], rtol=1e-14)
+    finally:
+        B.bf_gc_plan_destroy(p)
+
+
+def test_fit_error_reports_convergence():
+    errs = []
+    for N in (4, 8, 12, 16, 20):
+        p = B.bf_gc_plan(8, 8, 1.0, 50.0, N)
+        errs.append(B.bf_gc_plan_info(p).fit_err)
+        B.bf_gc_plan_destroy(p)
+    assert all(b < a for a, b in zip(errs, errs[1:])) and errs[-1] < 1e-8
+
+
+def test_direct_rejects_bad_arguments_without_launching():
+    assert B.lib().bf_direct(0, 4, 1.0, 1.0, ctypes.c_void_p(256), ctypes.c_void_p(256), None) == B.BF_ERR_INVALID_ARG
+    assert B.lib().bf_direct(4, 4, 1.0, 1.0, ctypes.c_void_p(258), ctypes.c_void_p(256), None) == B.BF_ERR_INVALID_ARG
