@@ -137,6 +137,29 @@ bf_status bf_gc_forward_host(bf_gc_plan_t plan, const float *h_f, float *h_out, 
 bf_status bf_gc_backward(bf_gc_plan_t plan, const float *d_f, const float *d_gout, float *d_gf,
                          double *d_gsigma_r, void *d_ws, size_t ws_bytes, bf_stream_t stream);
 
+/* Forward filter that allocates nothing and takes no workspace (the paper has no
+ * counterpart; this is a deployment aid).
+ *
+ * Some callers cannot allocate device memory at the time they filter: a plug-in
+ * running inside a host application that owns the device allocator, or a real-time
+ * pipeline that forbids cudaMalloc after start-up because it may synchronise the
+ * device.  This entry point runs the same forward as bf_gc_forward but uses a fixed
+ * scratch area of BF_STATIC_SCRATCH_BYTES bytes kept in the library's own device
+ * memory (a file-scope __device__ array: every GPU that loads the library holds it
+ * until the process exits).  The caller still passes d_f and d_out.
+ *  - If the plan's forward workspace (bf_gc_workspace_size) exceeds
+ *    BF_STATIC_SCRATCH_BYTES, returns BF_ERR_WORKSPACE and enqueues nothing.
+ *  - The first call on a device looks up the array's device address with that device
+ *    current (the current device is used, and `stream` must belong to it); make that
+ *    first call before any stream capture.
+ *  - All calls share the one scratch area, which keeps the last call's contents (the
+ *    forward rewrites all of it that it reads).  Calls whose execution overlaps on the
+ *    GPU (other streams, other plans) race on it and give wrong results: order them.
+ *  - Calls no allocation routine; bf_gc_diagnostics cannot read this scratch. */
+#define BF_STATIC_SCRATCH_BYTES (64u << 20)
+bf_status bf_gc_forward_static(bf_gc_plan_t plan, const float *d_f, float *d_out,
+                               bf_stream_t stream);
+
 /* Read back the diagnostics of the last forward that used d_ws (synchronises stream). */
 bf_status bf_gc_diagnostics(bf_gc_plan_t plan, const void *d_ws, bf_gc_diag *out,
                             bf_stream_t stream);

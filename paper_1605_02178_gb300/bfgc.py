@@ -54,6 +54,7 @@ SIGNATURES = {
     "bf_gc_workspace_size": (_I, [_P, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
     "bf_gc_forward": (_I, [_P, _P, _P, _P, _SZ, _P]),
     "bf_gc_forward_host": (_I, [_P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "bf_gc_forward_static": (_I, [_P, _P, _P, _P]),
     "bf_gc_backward": (_I, [_P, _P, _P, _P, _P, _P, _SZ, _P]),
     "bf_gc_diagnostics": (_I, [_P, _P, ctypes.POINTER(bf_gc_diag), _P]),
     "bf_gc_plan_destroy": (None, [_P]),
@@ -154,6 +155,17 @@ def bf_gc_forward_host(plan, h_f, h_out, d_f, d_out, ws, stream=None):
     _check(lib().bf_gc_forward_host(plan, _ptr(h_f), _ptr(h_out), _ptr(d_f), _ptr(d_out), _ptr(ws),
                                     ws.numel() * ws.element_size(), _stream(stream)), "bf_gc_forward_host")
     return h_out
+
+
+BF_STATIC_SCRATCH_BYTES = 64 << 20
+
+
+def bf_gc_forward_static(plan, f, out, stream=None):
+    """Forward with the library's fixed device scratch; allocates nothing (see bfgc.h)."""
+    _dev_f32(f, "f")
+    _dev_f32(out, "out")
+    _check(lib().bf_gc_forward_static(plan, _ptr(f), _ptr(out), _stream(stream)), "bf_gc_forward_static")
+    return out
 
 
 def bf_gc_backward(plan, f, gout, gf, gsigma_r, ws, stream=None):
