@@ -74,10 +74,22 @@ __global__ void __launch_bounds__(256) k_hpass(const float* __restrict__ X, floa
     const int tid = threadIdx.x;
 
     for (int d = tid; d < T; d += blockDim.x) g[d] = d <= 2 * R ? t.g[abs(d - R)] : 0.0f;
-    for (int idx = tid; idx < HP_ROWS * LEN; idx += blockDim.x) {
-        const int r = idx / LEN, k = idx - r * LEN;
-        const int y = y0 + r;
-        s[r * PITCH + k] = y < H ? src[(size_t)y * W + mirror(x0 - R + k, W)] : 0.0f;
+    {
+        // warp w loads rows w, w+8, ...; lanes stride along the row (mirror only at the edges)
+        const int lane = tid & 31, warp = tid >> 5;
+        for (int r = warp; r < HP_ROWS; r += 8) {
+            const int y = y0 + r;
+            float* srow = s + r * PITCH;
+            if (y < H) {
+                const float* grow = src + (size_t)y * W;
+                for (int k = lane; k < LEN; k += 32) {
+                    const int x = x0 - R + k;
+                    srow[k] = grow[(unsigned)x < (unsigned)W ? x : mirror(x, W)];
+                }
+            } else {
+                for (int k = lane; k < LEN; k += 32) srow[k] = 0.0f;
+            }
+        }
     }
     __syncthreads();
 
@@ -90,21 +102,18 @@ __global__ void __launch_bounds__(256) k_hpass(const float* __restrict__ X, floa
         float acc[8];
 #pragma unroll
         for (int v = 0; v < 8; ++v) acc[v] = 0.0f;
-        float w0[8], w1[8];
-        *reinterpret_cast<float4*>(&w0[0]) = *reinterpret_cast<const float4*>(srow + xb);
-        *reinterpret_cast<float4*>(&w0[4]) = *reinterpret_cast<const float4*>(srow + xb + 4);
         for (int d0 = 0; d0 < T; d0 += 8) {
+            float w0[8], w1[8], gg[8];
+            *reinterpret_cast<float4*>(&w0[0]) = *reinterpret_cast<const float4*>(srow + xb + d0);
+            *reinterpret_cast<float4*>(&w0[4]) = *reinterpret_cast<const float4*>(srow + xb + 4 + d0);
             *reinterpret_cast<float4*>(&w1[0]) = *reinterpret_cast<const float4*>(srow + xb + 8 + d0);
             *reinterpret_cast<float4*>(&w1[4]) = *reinterpret_cast<const float4*>(srow + xb + 12 + d0);
-            float gg[8];
             *reinterpret_cast<float4*>(&gg[0]) = *reinterpret_cast<const float4*>(g + d0);
             *reinterpret_cast<float4*>(&gg[4]) = *reinterpret_cast<const float4*>(g + d0 + 4);
 #pragma unroll
             for (int j = 0; j < 8; ++j)
 #pragma unroll
                 for (int v = 0; v < 8; ++v) acc[v] = fmaf(gg[j], (v + j < 8) ? w0[v + j] : w1[v + j - 8], acc[v]);
-#pragma unroll
-            for (int v = 0; v < 8; ++v) w0[v] = w1[v];
         }
         res[2 * vb] = make_float4(acc[0], acc[1], acc[2], acc[3]);
         res[2 * vb + 1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
@@ -154,10 +163,12 @@ __global__ void __launch_bounds__(256) k_vpass(const float* __restrict__ X, floa
     const int tid = threadIdx.x;
 
     for (int d = tid; d < T; d += blockDim.x) g[d] = d <= 2 * R ? t.g[abs(d - R)] : 0.0f;
-    for (int idx = tid; idx < LEN * VP_COLS; idx += blockDim.x) {
-        const int r = idx / VP_COLS, c = idx - r * VP_COLS;
-        const int x = x0 + c;
-        s[idx] = x < W ? src[(size_t)mirror(y0 - R + r, H) * W + x] : 0.0f;
+    {
+        const int c = tid & (VP_COLS - 1), x = x0 + c;
+        for (int r = tid / VP_COLS; r < LEN; r += 256 / VP_COLS) {
+            const int y = y0 - R + r;
+            s[r * VP_COLS + c] = x < W ? src[(size_t)((unsigned)y < (unsigned)H ? y : mirror(y, H)) * W + x] : 0.0f;
+        }
     }
     __syncthreads();
 
@@ -165,24 +176,22 @@ __global__ void __launch_bounds__(256) k_vpass(const float* __restrict__ X, floa
 #pragma unroll
     for (int vb = 0; vb < 2; ++vb) {
         const int rb = rg * 16 + vb * 8;
-        float acc[8], w0[8], w1[8];
+        float acc[8];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
-            acc[v] = 0.0f;
-            w0[v] = s[(rb + v) * VP_COLS + c];
-        }
+        for (int v = 0; v < 8; ++v) acc[v] = 0.0f;
         for (int d0 = 0; d0 < T; d0 += 8) {
+            float w0[8], w1[8], gg[8];
 #pragma unroll
-            for (int v = 0; v < 8; ++v) w1[v] = s[(rb + 8 + d0 + v) * VP_COLS + c];
-            float gg[8];
+            for (int v = 0; v < 8; ++v) {
+                w0[v] = s[(rb + d0 + v) * VP_COLS + c];
+                w1[v] = s[(rb + 8 + d0 + v) * VP_COLS + c];
+            }
             *reinterpret_cast<float4*>(&gg[0]) = *reinterpret_cast<const float4*>(g + d0);
             *reinterpret_cast<float4*>(&gg[4]) = *reinterpret_cast<const float4*>(g + d0 + 4);
 #pragma unroll
             for (int j = 0; j < 8; ++j)
 #pragma unroll
                 for (int v = 0; v < 8; ++v) acc[v] = fmaf(gg[j], (v + j < 8) ? w0[v + j] : w1[v + j - 8], acc[v]);
-#pragma unroll
-            for (int v = 0; v < 8; ++v) w0[v] = w1[v];
         }
         const int x = x0 + c;
 #pragma unroll

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "bfgc_internal.h"
+#include "bfgc_tc.h"
 
 namespace {
 
@@ -132,6 +133,8 @@ size_t fwd_workspace(const bf_gc_plan_s* p) {
     switch (p->form) {
     case BF_FORM_PLAIN:
         return BF_WS_HEADER + 2 * (size_t)p->C * bfgc::plain_plane_stride(p->H, p->W) * sizeof(float);
+    case BF_FORM_FUSED_TC:
+        return BF_WS_HEADER + round_up(bfgc::tc_workspace_bytes(bfgc::tc_geometry(p->H, p->W, p->R, p->C), p->C), 256);
     default:
         return 0;
     }
@@ -146,6 +149,8 @@ bool form_supported(const bf_gc_plan_s* p) {
     switch (p->form) {
     case BF_FORM_PLAIN:
         return p->precision == BF_PREC_FP32;
+    case BF_FORM_FUSED_TC:
+        return (p->precision == BF_PREC_BF16 || p->precision == BF_PREC_FP16) && bfgc::tc_supported(p->R, p->C);
     default:
         return false;
     }
@@ -296,6 +301,15 @@ bf_status bf_gc_forward(bf_gc_plan_t p, const float* f, float* out, void* ws, si
         if ((e = bfgc::launch_vpass(Y, X, p->gp, p->taps, cs, p->C, s)) != cudaSuccess) break;
         prof_mark(p, "combine", s);
         e = bfgc::launch_combine(f, X, out, p->gp, cs, diag, s);
+        break;
+    }
+    case BF_FORM_FUSED_TC: {
+        const bfgc::TcGeom g = bfgc::tc_geometry(p->H, p->W, p->R, p->C);
+        const bool fp16 = p->precision == BF_PREC_FP16;
+        prof_mark(p, "build_hpass_tc", s);
+        if ((e = bfgc::launch_build_hpass_tc(f, body, p->gp, p->taps, g, fp16, s)) != cudaSuccess) break;
+        prof_mark(p, "vpass_combine_tc", s);
+        e = bfgc::launch_vpass_combine_tc(f, body, out, p->gp, p->taps, g, fp16, diag, s);
         break;
     }
     default:

@@ -129,3 +129,63 @@ def test_uhd_sampled_outputs_match_oracle():
     ref = oracle.gcf_at(f, idx, 10.0, 50.0, 20)
     err = np.abs(out.reshape(-1)[idx] - ref).max()
     assert err <= 1e-3, err
+
+
+# ----------------------------------------------------------------------------- fused tensor-core form
+# Stated tolerance for BF16 channel storage: 0.5 max-abs on [0, 255].  FP16 keeps 3 more
+# mantissa bits; on the convergent (sigma_r >= 40) cases it is held to 0.05.
+TC_CASES = [c for c in CONDITIONED if c[3] >= 40.0] + [(200, 300, 32.0, 50.0, 12), (150, 170, 20.0, 60.0, 8)]
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16", 0.5), ("fp16", 0.05)])
+@pytest.mark.parametrize("H,W,ss,sr,N", TC_CASES)
+def test_fused_tc_forward_matches_oracle(H, W, ss, sr, N, prec, tol):
+    f = _image(H, W, seed=H * 1000 + W)
+    ref, aux = oracle.gcf(f, ss, sr, N, return_pq=True)
+    out, plan = _gpu_forward(f, ss, sr, N, form="fused_tc", precision=prec)
+    cond = aux["Qabs"] / np.maximum(np.abs(aux["Q"]), 1e-300)
+    mask = cond <= 1e4
+    err = np.abs(out - ref)[mask].max()
+    assert err <= tol, f"{prec} max-abs {err}"
+    d = plan.diagnostics()
+    assert d["n_guarded"] == 0 and d["error_flags"] == 0
+
+
+def test_fused_tc_fp16_at_paper_operating_point():
+    """sigma_r = 30, N = 28 (Table 2): FP16 storage stays within 0.5."""
+    f = _image(130, 70, seed=130070)
+    ref = oracle.gcf(f, 3.0, 30.0, 28)
+    out, _ = _gpu_forward(f, 3.0, 30.0, 28, form="fused_tc", precision="fp16")
+    assert np.abs(out - ref).max() <= 0.5
+
+
+@pytest.mark.xfail(strict=True, reason="BF16 channel storage exceeds the 0.5 bound at sigma_r=30, N=28 "
+                                       "(measured 0.67 on this image); FP16 meets it")
+def test_fused_tc_bf16_at_paper_operating_point():
+    f = _image(130, 70, seed=130070)
+    ref = oracle.gcf(f, 3.0, 30.0, 28)
+    out, _ = _gpu_forward(f, 3.0, 30.0, 28, form="fused_tc", precision="bf16")
+    assert np.abs(out - ref).max() <= 0.5
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16", 0.5), ("fp16", 0.05)])
+def test_fused_tc_uhd_sampled_outputs(prec, tol):
+    f = synth.workload("uhd")["f"]
+    H, W = f.shape
+    out, plan = _gpu_forward(f, 10.0, 50.0, 20, form="fused_tc", precision=prec)
+    rng = np.random.default_rng(1)
+    ys = np.concatenate([[0, 0, H - 1, H - 1, 1, H - 2, H // 2], rng.integers(0, H, 60)])
+    xs = np.concatenate([[0, W - 1, 0, W - 1, W // 2, 3, W - 5], rng.integers(0, W, 60)])
+    idx = ys * W + xs
+    ref = oracle.gcf_at(f, idx, 10.0, 50.0, 20)
+    assert np.abs(out.reshape(-1)[idx] - ref).max() <= tol
+
+
+def test_fused_tc_matches_plain_on_constant_and_flips():
+    out, _ = _gpu_forward(np.full((70, 90), 201.25, dtype=np.float32), 3.0, 50.0, 12, form="fused_tc",
+                          precision="fp16")
+    assert np.abs(out - 201.25).max() <= 0.05
+    f = _image(80, 100, seed=9)
+    a, _ = _gpu_forward(f, 3.0, 50.0, 12, form="fused_tc", precision="fp16")
+    b, _ = _gpu_forward(np.ascontiguousarray(f[::-1, ::-1]), 3.0, 50.0, 12, form="fused_tc", precision="fp16")
+    assert np.abs(a - b[::-1, ::-1]).max() <= 0.05
