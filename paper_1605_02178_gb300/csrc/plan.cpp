@@ -8,6 +8,7 @@
 #include <new>
 #include <vector>
 
+#include "bfgc_adjoint.h"
 #include "bfgc_internal.h"
 #include "bfgc_tc.h"
 
@@ -140,9 +141,12 @@ size_t fwd_workspace(const bf_gc_plan_s* p) {
     }
 }
 
+// Backward workspace (every form): header | X: C planes | Y: C planes | D: one plane |
+// 2 * kAdjBlocks doubles.  Its prefix is the plain forward's workspace, so a plain forward
+// with BF_OPT_SAVE_CHANNELS = 1 run on the same buffer leaves the filtered channels in X.
 size_t bwd_workspace(const bf_gc_plan_s* p) {
-    (void)p;
-    return 0;
+    const size_t cs = bfgc::plain_plane_stride(p->H, p->W);
+    return BF_WS_HEADER + (2 * (size_t)p->C + 1) * cs * sizeof(float) + 2 * bfgc::kAdjBlocks * sizeof(double);
 }
 
 bool form_supported(const bf_gc_plan_s* p) {
@@ -335,9 +339,48 @@ bf_status bf_gc_forward_host(bf_gc_plan_t p, const float* h_f, float* h_out, flo
 
 bf_status bf_gc_backward(bf_gc_plan_t p, const float* f, const float* gout, float* gf,
                          double* gsigma, void* ws, size_t ws_bytes, bf_stream_t stream) {
-    (void)f; (void)gout; (void)gf; (void)gsigma; (void)ws; (void)ws_bytes; (void)stream;
-    if (!p) return BF_ERR_INVALID_ARG;
-    return BF_ERR_UNSUPPORTED;
+    if (!p || !f || !gout || !gf || !aligned(f, 16) || !aligned(gout, 16) || !aligned(gf, 16) ||
+        (gsigma && !aligned(gsigma, 8)))
+        return BF_ERR_INVALID_ARG;
+    if (!form_supported(p)) return BF_ERR_UNSUPPORTED;
+    if (!ws || !aligned(ws, 256) || ws_bytes < bwd_workspace(p)) return BF_ERR_WORKSPACE;
+    p->used = true;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t cs = bfgc::plain_plane_stride(p->H, p->W);
+    float* X = (float*)((char*)ws + BF_WS_HEADER);
+    float* Y = X + (size_t)p->C * cs;
+    float* Dt = Y + (size_t)p->C * cs;
+    double* partial = (double*)(Dt + cs);
+    bfgc::AdjCoef ac{};
+    for (int n = 0; n <= p->N; ++n) ac.dcoef[n] = (float)p->dcoef_dsigma[n];
+    ac.inv_sigma3 = 1.0 / (p->sigma_r * p->sigma_r * p->sigma_r);
+    cudaError_t e = cudaSuccess;
+    do {
+        if (!(p->save_channels && p->form == BF_FORM_PLAIN)) {      // filtered channels -> X
+            prof_mark(p, "build", s);
+            if ((e = bfgc::launch_build(f, X, p->gp, cs, s)) != cudaSuccess) break;
+            prof_mark(p, "hpass", s);
+            if ((e = bfgc::launch_hpass(X, Y, p->gp, p->taps, cs, p->C, s)) != cudaSuccess) break;
+            prof_mark(p, "vpass", s);
+            if ((e = bfgc::launch_vpass(Y, X, p->gp, p->taps, cs, p->C, s)) != cudaSuccess) break;
+        }
+        prof_mark(p, "adjoint_lambda", s);
+        if ((e = bfgc::launch_adjoint_lambda(f, gout, X, Y, Dt, partial, p->gp, ac, cs, s)) != cudaSuccess) break;
+        prof_mark(p, "adjoint_vpass", s);       // K = V H, so K^T = H^T V^T
+        if ((e = bfgc::launch_adjoint_pass(1, Y, X, p->gp, p->taps, cs, p->C, s)) != cudaSuccess) break;
+        prof_mark(p, "adjoint_hpass", s);
+        if ((e = bfgc::launch_adjoint_pass(0, X, Y, p->gp, p->taps, cs, p->C, s)) != cudaSuccess) break;
+        prof_mark(p, "adjoint_assemble", s);
+        if ((e = bfgc::launch_adjoint_assemble(f, Y, Dt, gf, partial + bfgc::kAdjBlocks, p->gp, ac, cs, s)) !=
+            cudaSuccess)
+            break;
+        if (gsigma) {
+            prof_mark(p, "adjoint_reduce", s);
+            e = bfgc::launch_adjoint_reduce(partial, 2 * bfgc::kAdjBlocks, gsigma, s);
+        }
+    } while (false);
+    prof_close(p, s);
+    return cuda_status(e);
 }
 
 bf_status bf_gc_diagnostics(bf_gc_plan_t p, const void* ws, bf_gc_diag* out, bf_stream_t stream) {
