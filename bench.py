@@ -30,7 +30,7 @@ N_INPUTS = 8
 L2_BYTES = 129 * 2 ** 20
 
 # candidate forms, best first; the first one the library supports is the headline
-FORMS = [("fused_tc", "bf16"), ("fused_tc", "fp16"), ("plain", "fp32")]
+FORMS = [("fused_tc", "bf16"), ("fused_tc", "fp16"), ("plain", "fp32"), ("recursive", "fp32")]
 
 
 def parse():
@@ -126,6 +126,9 @@ def kernel_model(form, precision, C, R):
     if form == "plain":
         return {"build": ("hbm", 4 + 4 * C), "hpass": ("alu", 2 * (2 * R + 1) * C),
                 "vpass": ("alu", 2 * (2 * R + 1) * C), "combine": ("hbm", 4 * C + 8)}
+    if form == "recursive":
+        return {"build": ("hbm", 4 + 4 * C), "iir_rows": ("hbm", 16 * C), "iir_cols": ("hbm", 16 * C),
+                "combine": ("hbm", 4 * C + 8)}
     return {"build_hpass_tc": ("hbm", 4 + s * C), "vpass_combine_tc": ("hbm", s * C + 8)}
 
 
@@ -261,11 +264,15 @@ def run_ours(args):
             out = plan.forward(base, torch.empty_like(base), plan.workspace("fwd", dev), stream)
             torch.cuda.synchronize(dev)
             o = out.cpu().numpy().astype(np.float64)
-            accuracy[f"{key[0]}/{key[1]}"] = {
-                "maxabs_vs_fp64_oracle_sampled": float(np.abs(o.reshape(-1)[idx] - ref).max()),
-                "samples": int(idx.size),
-                "psnr_vs_exact_db": oracle.psnr_db(o, exact_np),
-            }
+            acc = {"psnr_vs_exact_db": oracle.psnr_db(o, exact_np)}
+            if key[0] == "recursive":
+                # a different spatial filter from eq. (7): its parity against the oracle's
+                # recursive twin is covered by the tests; here only the PSNR is reported
+                acc["note"] = "recursive (Young-van Vliet) spatial filter"
+            else:
+                acc["maxabs_vs_fp64_oracle_sampled"] = float(np.abs(o.reshape(-1)[idx] - ref).max())
+                acc["samples"] = int(idx.size)
+            accuracy[f"{key[0]}/{key[1]}"] = acc
 
     # ---- end to end through the C ABI with host buffers (pinned), headline form
     plan = plans[headline]

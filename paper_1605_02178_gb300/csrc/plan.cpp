@@ -10,6 +10,7 @@
 
 #include "bfgc_adjoint.h"
 #include "bfgc_internal.h"
+#include "bfgc_recursive.h"
 #include "bfgc_tc.h"
 
 namespace {
@@ -136,9 +137,30 @@ size_t fwd_workspace(const bf_gc_plan_s* p) {
         return BF_WS_HEADER + 2 * (size_t)p->C * bfgc::plain_plane_stride(p->H, p->W) * sizeof(float);
     case BF_FORM_FUSED_TC:
         return BF_WS_HEADER + round_up(bfgc::tc_workspace_bytes(bfgc::tc_geometry(p->H, p->W, p->R, p->C), p->C), 256);
+    case BF_FORM_RECURSIVE:
+        return BF_WS_HEADER + 2 * (size_t)p->C * bfgc::plain_plane_stride(p->H, p->W) * sizeof(float) +
+               (size_t)p->C * std::max(p->H, p->W) * p->R * sizeof(float);
     default:
         return 0;
     }
+}
+
+// Young and van Vliet (1995): scale q from sigma by their fit, b0..b3 cubic in q,
+// B = 1 - (b1 + b2 + b3)/b0; the recursion uses a_k = b_k / b0.
+bfgc::IirCoef iir_coefficients(double sigma, int P) {
+    const double q = sigma >= 2.5 ? 0.98711 * sigma - 0.96330 : 3.97156 - 4.14554 * sqrt(1.0 - 0.26891 * sigma);
+    const double q2 = q * q, q3 = q2 * q;
+    const double b0 = 1.57825 + 2.44413 * q + 1.4281 * q2 + 0.422205 * q3;
+    const double b1 = 2.44413 * q + 2.85619 * q2 + 1.26661 * q3;
+    const double b2 = -(1.4281 * q2 + 1.26661 * q3);
+    const double b3 = 0.422205 * q3;
+    bfgc::IirCoef c;
+    c.P = P;
+    c.B = (float)(1.0 - (b1 + b2 + b3) / b0);
+    c.a1 = (float)(b1 / b0);
+    c.a2 = (float)(b2 / b0);
+    c.a3 = (float)(b3 / b0);
+    return c;
 }
 
 // Backward workspace (every form): header | X: C planes | Y: C planes | D: one plane |
@@ -155,6 +177,8 @@ bool form_supported(const bf_gc_plan_s* p) {
         return p->precision == BF_PREC_FP32;
     case BF_FORM_FUSED_TC:
         return (p->precision == BF_PREC_BF16 || p->precision == BF_PREC_FP16) && bfgc::tc_supported(p->R, p->C);
+    case BF_FORM_RECURSIVE:
+        return p->precision == BF_PREC_FP32 && p->sigma_s >= 0.5;
     default:
         return false;
     }
@@ -316,6 +340,22 @@ bf_status bf_gc_forward(bf_gc_plan_t p, const float* f, float* out, void* ws, si
         e = bfgc::launch_vpass_combine_tc(f, body, out, p->gp, p->taps, g, fp16, diag, s);
         break;
     }
+    case BF_FORM_RECURSIVE: {
+        const size_t cs = bfgc::plain_plane_stride(p->H, p->W);
+        float* X = (float*)body;
+        float* Y = X + (size_t)p->C * cs;
+        float* tail = Y + (size_t)p->C * cs;
+        const bfgc::IirCoef ic = iir_coefficients(p->sigma_s, p->R);
+        prof_mark(p, "build", s);
+        if ((e = bfgc::launch_build(f, X, p->gp, cs, s)) != cudaSuccess) break;
+        prof_mark(p, "iir_rows", s);
+        if ((e = bfgc::launch_iir(0, X, Y, tail, p->gp, ic, cs, p->C, s)) != cudaSuccess) break;
+        prof_mark(p, "iir_cols", s);
+        if ((e = bfgc::launch_iir(1, Y, X, tail, p->gp, ic, cs, p->C, s)) != cudaSuccess) break;
+        prof_mark(p, "combine", s);
+        e = bfgc::launch_combine(f, X, out, p->gp, cs, diag, s);
+        break;
+    }
     default:
         return BF_ERR_UNSUPPORTED;
     }
@@ -342,7 +382,7 @@ bf_status bf_gc_backward(bf_gc_plan_t p, const float* f, const float* gout, floa
     if (!p || !f || !gout || !gf || !aligned(f, 16) || !aligned(gout, 16) || !aligned(gf, 16) ||
         (gsigma && !aligned(gsigma, 8)))
         return BF_ERR_INVALID_ARG;
-    if (!form_supported(p)) return BF_ERR_UNSUPPORTED;
+    if (!form_supported(p) || p->form == BF_FORM_RECURSIVE) return BF_ERR_UNSUPPORTED;
     if (!ws || !aligned(ws, 256) || ws_bytes < bwd_workspace(p)) return BF_ERR_WORKSPACE;
     p->used = true;
     cudaStream_t s = (cudaStream_t)stream;

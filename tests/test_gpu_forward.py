@@ -189,3 +189,30 @@ def test_fused_tc_matches_plain_on_constant_and_flips():
     a, _ = _gpu_forward(f, 3.0, 50.0, 12, form="fused_tc", precision="fp16")
     b, _ = _gpu_forward(np.ascontiguousarray(f[::-1, ::-1]), 3.0, 50.0, 12, form="fused_tc", precision="fp16")
     assert np.abs(a - b[::-1, ::-1]).max() <= 0.05
+
+
+# ----------------------------------------------------------------------------- recursive form
+@pytest.mark.parametrize("H,W,ss,sr,N", [(97, 131, 2.0, 50.0, 12), (64, 200, 5.0, 60.0, 10),
+                                         (40, 33, 10.0, 50.0, 16), (1, 37, 2.0, 50.0, 12),
+                                         (5, 3, 3.0, 50.0, 12), (150, 170, 20.0, 60.0, 8),
+                                         (96, 96, 0.7, 50.0, 12)])
+def test_recursive_forward_matches_oracle_twin(H, W, ss, sr, N):
+    """Young-van Vliet recursive spatial filter: FP32 GPU against the FP64 oracle running
+    the same recursion, padding and initialisation."""
+    f = _image(H, W, seed=H * 7 + W)
+    ref, aux = oracle.gcf(f, ss, sr, N, spatial="recursive", return_pq=True)
+    out, plan = _gpu_forward(f, ss, sr, N, form="recursive")
+    cond = aux["Qabs"] / np.maximum(np.abs(aux["Q"]), 1e-300)
+    mask = cond <= 1e4
+    assert np.abs(out - ref)[mask].max() <= 1e-3
+    exact = oracle.exact_bf(f, ss, sr)
+    print(f"recursive {H}x{W} sigma_s={ss}: PSNR vs exact {oracle.psnr_db(out, exact):.1f} dB "
+          f"(direct form {oracle.psnr_db(oracle.gcf(f, ss, sr, N), exact):.1f} dB)")
+
+
+def test_recursive_form_has_no_backward():
+    f = torch.from_numpy(_image(32, 32, seed=1)).cuda()
+    plan = api.GCPlan(32, 32, 2.0, 50.0, 8, form="recursive")
+    with pytest.raises(bfgc.BfError) as e:
+        plan.backward(f, torch.ones_like(f))
+    assert e.value.status == bfgc.BF_ERR_UNSUPPORTED
