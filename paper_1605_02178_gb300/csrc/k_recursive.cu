@@ -61,7 +61,6 @@ __global__ void __launch_bounds__(32) k_iir_rows(const float* __restrict__ X, fl
     const bool live = myrow < p.H;
     const float* src = X + (size_t)plane * cs;
     float* dst = Y + (size_t)plane * cs;
-    float* tl = tail + ((size_t)plane * p.H + (live ? myrow : 0)) * (size_t)P;
     const int ext = n + 2 * P;
     const int chunks = (ext + IR_TILE - 1) / IR_TILE;
 
@@ -128,7 +127,6 @@ __global__ void __launch_bounds__(32) k_iir_rows(const float* __restrict__ X, fl
         }
         __syncwarp();
     }
-    (void)tl;
 }
 
 // ---------------------------------------------------------------------------------------

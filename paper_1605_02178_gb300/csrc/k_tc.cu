@@ -1,19 +1,20 @@
-// Fused tensor-core form of the fast algorithm.
+// Column pass of eq. (7) + ratio (eqs. (8)-(10)) of the fused tensor-core form.
 //
-//   k_build_hpass_tc : f -> channels e*u^n (eq. (6), centring eq. (17)) generated in shared
-//                      memory as BF16/FP16, then the row pass of eq. (7) as a banded
-//                      Toeplitz product on the tensor cores; writes the row-filtered
-//                      channels Y[c][p][x] (p = padded row, image row p - P, mirrored).
-//   k_vpass_combine_tc : per channel (highest first) the column pass of eq. (7) as a banded
-//                      Toeplitz product with Y tiles fed by TMA through an mbarrier ring,
-//                      then Horner accumulation of P and Q (eqs. (8)-(9)) in registers and
-//                      the guarded ratio (eq. (10)) with un-centring.
+//   k_vpass_combine_tc : per channel (highest first) the column pass as a banded Toeplitz
+//                        product on mma.sync tiles, the row-filtered channel tile fed by TMA
+//                        through an mbarrier ring filled by a producer warp; Horner
+//                        accumulation of P and Q in registers, then the guarded ratio and
+//                        un-centring.  (The row pass is k_umma.cu.)
 //
-// Banded Toeplitz product.  With k-blocks of 16 input samples and output blocks of 16,
-// output block j only meets k-blocks j-a .. j+a (a = ceil(R/16)); the 16x16 (or 16x8)
-// Toeplitz fragments depend only on the offset o = kb - j, so the (2a+1) fragments of the
-// spatial kernel stay in registers for the whole kernel.  Work per output and channel:
-// 16 (2a+1) multiply-adds against the 2R+1 of the direct sum (80 vs 61 at R = 30).
+// Banded Toeplitz product.  With k-blocks of 16 input rows and output blocks of 16 rows,
+// output block j only meets k-blocks j-a .. j+a (a = ceil(R/16)); the 16x16 Toeplitz
+// fragments depend only on the offset o = kb - j, so the (2a+1) fragments of the spatial
+// kernel stay in registers.  Work per output and channel: 16 (2a+1) multiply-adds against
+// the 2R+1 of the direct sum (80 vs 61 at R = 30).
+//
+// Row-filtered channels Y are stored row-interleaved, Y[p][c][x] (padded row p, channel c,
+// column x): the row pass writes consecutive (row, channel) product rows to consecutive
+// memory rows, and the column pass reads one channel's rows with a 3-D TMA box.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -60,143 +61,18 @@ __device__ __forceinline__ void mma16816<__half>(float* d, const uint32_t* a, ui
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void ldmatrix_x4(uint32_t* r, uint32_t addr) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr));
-}
 __device__ __forceinline__ void ldmatrix_x4_trans(uint32_t* r, uint32_t addr) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr));
 }
 
-// spatial tap at signed offset d (zero outside the window)
-__device__ __forceinline__ float tap(const Taps& t, int d) {
-    const int ad = d < 0 ? -d : d;
-    return ad <= t.R ? t.g[ad] : 0.0f;
-}
-
-// ----------------------------------------------------------------------------- kernel A
-// Tile: TR padded rows x 256 output columns.  Shared memory holds the channels of the
-// TR rows over the columns x0 - 16a .. x0 + 256 + 16a as an M x K matrix, M = TR*C rows
-// (row m = r*C + c), K = 256 + 32a columns, row pitch padded by 16 bytes so that the 8
-// row addresses of an ldmatrix fall in distinct bank groups.
-constexpr int KA_COLS = 256;
-
-__host__ __device__ inline int ka_kcols(int a) { return KA_COLS + 32 * a; }
-__host__ __device__ inline int ka_pitch_bytes(int a) { return ka_kcols(a) * 2 + 16; }
-
-template <typename T, int A>
-__global__ void __launch_bounds__(256) k_build_hpass_tc(const float* __restrict__ f, T* __restrict__ Y,
-                                                        const GcParams p, const Taps t, TcGeom g) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int TR = g.ka_rows, C = p.C;
-    const int M = TR * C, MP = (M + 15) & ~15;
-    const int KC = ka_kcols(A), PB = ka_pitch_bytes(A);
-    const int p0 = blockIdx.y * TR;                 // first padded row of the tile
-    const int x0 = blockIdx.x * KA_COLS;
-
-    // ---- channels into shared memory: two columns per thread-iteration
-    const int pairs = KC / 2;
-    for (int idx = tid; idx < TR * pairs; idx += blockDim.x) {
-        const int r = idx / pairs, kp = idx - r * pairs;
-        const int pr = p0 + r;
-        unsigned char* row = smem + (size_t)(r * C) * PB + kp * 4;
-        if (pr >= g.Hp) {
-            for (int c = 0; c < C; ++c) *reinterpret_cast<uint32_t*>(row + (size_t)c * PB) = 0u;
-            continue;
-        }
-        int y = pr - g.P;
-        y = (unsigned)y < (unsigned)p.H ? y : mirror(y, p.H);
-        const float* frow = f + (size_t)y * p.W;
-        int xa = x0 - 16 * A + 2 * kp, xb = xa + 1;
-        xa = (unsigned)xa < (unsigned)p.W ? xa : mirror(xa, p.W);
-        xb = (unsigned)xb < (unsigned)p.W ? xb : mirror(xb, p.W);
-        const float ua = (__ldg(frow + xa) - p.t_c) * p.inv_sr, ub = (__ldg(frow + xb) - p.t_c) * p.inv_sr;
-        float va = expf(-p.half_mu * ua * ua), vb = expf(-p.half_mu * ub * ub);
-        for (int c = 0; c < C; ++c) {
-            *reinterpret_cast<uint32_t*>(row + (size_t)c * PB) = Pack<T>::two(va, vb);
-            va *= ua;
-            vb *= ub;
-        }
-    }
-    for (int idx = tid; idx < (MP - M) * (PB / 4); idx += blockDim.x) {
-        const int r = M + idx / (PB / 4), w = idx % (PB / 4);
-        reinterpret_cast<uint32_t*>(smem + (size_t)r * PB)[w] = 0u;
-    }
-
-    // ---- Toeplitz B fragments: B[k][n] = g(16(o - a) + k - 8h - n), o = 0..2a, h = 0, 1
-    uint32_t bf[2 * A + 1][2][2];
-    {
-        const int gn = lane >> 2, tk = (lane & 3) * 2;
-#pragma unroll
-        for (int o = 0; o <= 2 * A; ++o)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int base = 16 * (o - A) - 8 * h - gn;
-                bf[o][h][0] = Pack<T>::two(tap(t, base + tk), tap(t, base + tk + 1));
-                bf[o][h][1] = Pack<T>::two(tap(t, base + tk + 8), tap(t, base + tk + 9));
-            }
-    }
-    __syncthreads();
-
-    // ---- MMA: items = (16-row M block, 64-column output group)
-    const int mblocks = MP / 16, items = mblocks * 4;
-    const uint32_t sbase = smem_u32(smem);
-    for (int it = warp; it < items; it += 8) {
-        const int mb = it >> 2, ng = it & 3;
-        float acc[4][2][4];
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj)
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) acc[jj][h][e] = 0.0f;
-        const uint32_t arow = sbase + (uint32_t)((mb * 16 + (lane & 15)) * PB) + (uint32_t)((lane >> 4) * 16);
-#pragma unroll
-        for (int i = 0; i < 4 + 2 * A; ++i) {
-            const int kb = 4 * ng + i;                        // local k-block
-            uint32_t af[4];
-            ldmatrix_x4(af, arow + (uint32_t)(kb * 32));
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                const int o = i - jj;
-                if (o >= 0 && o <= 2 * A) {
-                    mma16816<T>(acc[jj][0], af, bf[o][0][0], bf[o][0][1]);
-                    mma16816<T>(acc[jj][1], af, bf[o][1][0], bf[o][1][1]);
-                }
-            }
-        }
-        // ---- epilogue: D rows -> (padded row, channel), columns -> output columns
-        const int gr = lane >> 2, tc2 = (lane & 3) * 2;
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int m = mb * 16 + gr + 8 * half;
-            if (m >= M) continue;
-            const int r = m / C, c = m - r * C;
-            const int pr = p0 + r;
-            if (pr >= g.Hp) continue;
-            T* yrow = Y + ((size_t)c * g.Hp + pr) * g.Wp;
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int x = x0 + 64 * ng + 16 * jj + 8 * h + tc2;
-                    if (x < g.Wp)
-                        *reinterpret_cast<uint32_t*>(yrow + x) =
-                            Pack<T>::two(acc[jj][h][2 * half], acc[jj][h][2 * half + 1]);
-                }
-        }
-    }
-}
-
-// ----------------------------------------------------------------------------- kernel B
-constexpr int KB_ROWS = 64, KB_COLS = 64;
-constexpr unsigned kSpinLimit = 1u << 21;      // bounded mbarrier waits (polls)
+// 13 warps (at most 4 per SM sub-partition, so 128 registers per thread are available):
+// warps 0..11 compute 32x16 pixels each of a 96x64 tile, warp 12 loads.
+constexpr int KB_ROWS = 96, KB_COLS = 64;
+constexpr int KB_CONSUMERS = 12;
+constexpr unsigned kSpinLimit = 1u << 21;          // bounded mbarrier waits (polls)
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(smem_u32(bar)), "r"(count));
@@ -204,6 +80,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" :: "r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" :: "r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     uint32_t ok;
@@ -218,24 +97,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int c, int y, uint64_t* bar) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
-        :: "r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n"
+        :: "r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(c), "r"(y), "r"(smem_u32(bar))
         : "memory");
 }
 
-// Shared layout: S stages of (64 + 32a) rows x 128 bytes (TMA 128-byte swizzle: the
-// 16-byte chunk j of row r sits at chunk j ^ (r & 7)), each 1024-byte aligned, then S
-// mbarriers.
+// Shared layout: S stages of (64 + 32a) rows x 128 bytes (TMA 128-byte swizzle: the 16-byte
+// chunk j of row r sits at chunk j ^ (r & 7)), each 1024-byte aligned; 2S mbarriers (full,
+// empty); the taps.
 __host__ __device__ inline int kb_tile_rows(int a) { return KB_ROWS + 32 * a; }
 __host__ __device__ inline int kb_stage_bytes(int a) { return kb_tile_rows(a) * 128; }
 
 template <typename T, int A>
-__global__ void __launch_bounds__(256) k_vpass_combine_tc(const __grid_constant__ CUtensorMap ymap,
-                                                          const float* __restrict__ f, float* __restrict__ out,
-                                                          const GcParams p, const Taps t, TcGeom g,
-                                                          DiagHeader* diag) {
+__global__ void __launch_bounds__(32 * (KB_CONSUMERS + 1), 1) k_vpass_combine_tc(
+    const __grid_constant__ CUtensorMap ymap, const float* __restrict__ f, float* __restrict__ out, const GcParams p,
+    const Taps t, TcGeom g, DiagHeader* diag) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // the 128-byte swizzle pattern repeats every 1024 bytes: align the stages to it
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -243,39 +121,67 @@ __global__ void __launch_bounds__(256) k_vpass_combine_tc(const __grid_constant_
     const int S = g.kb_stages, C = p.C;
     const int ROWS = kb_tile_rows(A), SB = kb_stage_bytes(A);
     const int box_rows = g.kb_box_rows, loads = ROWS / box_rows;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S * SB);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * SB);
+    uint64_t* empty = full + S;
+    float* gs = reinterpret_cast<float*>(empty + S);       // taps g[|d|], d = 0 .. 16(a+1)
     const int x0 = blockIdx.x * KB_COLS, y0 = blockIdx.y * KB_ROWS;
 
-    // channel m of the tile lives at Y rows m*Hp + y0 .. + ROWS (padded rows start P above)
-    auto issue = [&](int m, int s) {
-        mbar_expect_tx(&bars[s], (unsigned)SB);
-        for (int l = 0; l < loads; ++l)
-            tma_load_2d(smem + (size_t)s * SB + (size_t)l * box_rows * 128, &ymap, x0,
-                        m * g.Hp + y0 + l * box_rows, &bars[s]);
-    };
+    for (int d = tid; d <= 16 * (A + 1); d += blockDim.x) gs[d] = d <= t.R ? t.g[d] : 0.0f;
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], KB_CONSUMERS);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        for (int s = 0; s < S && s < C; ++s) issue(C - 1 - s, s);
+    }
+    __syncthreads();
+
+    // ---------------------------------------------------------------- producer warp
+    if (warp == KB_CONSUMERS) {
+        if (lane == 0) {
+            bool ok = true;
+            int issued = 0;
+            for (int i = 0; i < C && ok; ++i) {
+                const int s = i % S, m = C - 1 - i;
+                if (i >= S && !mbar_wait(&empty[s], (unsigned)(((i / S) - 1) & 1))) {
+                    ok = false;
+                    atomicOr(&diag->error_flags, 1u);
+                    break;
+                }
+                mbar_expect_tx(&full[s], (unsigned)SB);
+                // padded rows y0 .. y0 + ROWS of channel m (image rows start P = 16a above)
+                for (int l = 0; l < loads; ++l)
+                    tma_load_3d(smem + (size_t)s * SB + (size_t)l * box_rows * 128, &ymap, x0, m,
+                                y0 + l * box_rows, &full[s]);
+                issued = i + 1;
+            }
+            // every load this CTA issued lands before it may exit (bounded)
+            for (int i = (issued > S ? issued - S : 0); i < issued; ++i)
+                mbar_wait(&full[i % S], (unsigned)((i / S) & 1));
+        }
+        return;
     }
 
-    // ---- Toeplitz A fragments: A[m][k] = g(16(o - a) + k - m), o = 0..2a
+    // ---------------------------------------------------------------- consumer warps
+    // Toeplitz A fragments: A[m][k] = g(16(o - a) + k - m), o = 0..2a
     uint32_t af[2 * A + 1][4];
     {
         const int gm = lane >> 2, tk = (lane & 3) * 2;
+        auto tp = [&](int d) { return gs[d < 0 ? -d : d]; };      // |d| <= 16(a+1)
 #pragma unroll
         for (int o = 0; o <= 2 * A; ++o) {
             const int base = 16 * (o - A) + tk - gm;
-            af[o][0] = Pack<T>::two(tap(t, base), tap(t, base + 1));
-            af[o][1] = Pack<T>::two(tap(t, base - 8), tap(t, base - 7));
-            af[o][2] = Pack<T>::two(tap(t, base + 8), tap(t, base + 9));
-            af[o][3] = Pack<T>::two(tap(t, base), tap(t, base + 1));
+            af[o][0] = Pack<T>::two(tp(base), tp(base + 1));
+            af[o][1] = Pack<T>::two(tp(base - 8), tp(base - 7));
+            af[o][2] = Pack<T>::two(tp(base + 8), tp(base + 9));
+            af[o][3] = Pack<T>::two(tp(base), tp(base + 1));
         }
     }
 
-    // ---- per-thread pixels: warp (rh, cq) owns rows 32rh.. +32, columns 16cq.. +16
-    const int rh = warp & 1, cq = warp >> 1;
+    // per-thread pixels: warp (rh, cq) owns rows 32rh.. +32, columns 16cq.. +16
+    constexpr int RG = KB_ROWS / 32;
+    static_assert(KB_CONSUMERS == RG * (KB_COLS / 16), "consumer warps must tile the output tile exactly");
+    const int rh = warp % RG, cq = warp / RG;
     const int gr = lane >> 2, tc2 = (lane & 3) * 2;
     RatioAcc px[2][2][4];                          // [m16 block][n8 half][fragment element]
 #pragma unroll
@@ -289,56 +195,47 @@ __global__ void __launch_bounds__(256) k_vpass_combine_tc(const __grid_constant_
                 const float fv = (y < p.H && x < p.W) ? __ldg(f + (size_t)y * p.W + x) : p.t_c;
                 px[mb][h][e].init((fv - p.t_c) * p.inv_sr);
             }
-    __syncthreads();                                // barrier init visible to all threads
 
     bool ok = true;
-    int i_fail = C;
+    const int lrow = (lane & 7) + ((lane >> 3) & 1) * 8, lchunk = 2 * cq + (lane >> 4);
     for (int i = 0; i < C; ++i) {
         const int m = C - 1 - i, s = i % S;
-        const unsigned parity = (unsigned)((i / S) & 1);
-        if (ok && !mbar_wait(&bars[s], parity)) {
+        if (ok && !mbar_wait(&full[s], (unsigned)((i / S) & 1))) {
             ok = false;
-            i_fail = i;
             atomicOr(&diag->error_flags, 1u);
         }
-        if (ok) {
-            float acc[2][2][4];
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        float acc[2][2][4];
 #pragma unroll
-            for (int mb = 0; mb < 2; ++mb)
+        for (int mb = 0; mb < 2; ++mb)
 #pragma unroll
-                for (int h = 0; h < 2; ++h)
+            for (int h = 0; h < 2; ++h)
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) acc[mb][h][e] = 0.0f;
-            const unsigned char* st = smem + (size_t)s * SB;
-            const int lrow = (lane & 7) + ((lane >> 3) & 1) * 8, lchunk = 2 * cq + (lane >> 4);
+                for (int e = 0; e < 4; ++e) acc[mb][h][e] = 0.0f;
+        const unsigned char* st = smem + (size_t)s * SB;
 #pragma unroll
-            for (int kk = 0; kk < 2 + 2 * A; ++kk) {
-                const int kb = 2 * rh + kk;
-                const int row = 16 * kb + lrow;
-                uint32_t b[4];
-                ldmatrix_x4_trans(b, smem_u32(st + row * 128 + ((lchunk ^ (row & 7)) << 4)));
+        for (int kk = 0; kk < 2 + 2 * A; ++kk) {
+            const int row = 16 * (2 * rh + kk) + lrow;
+            uint32_t b[4];
+            ldmatrix_x4_trans(b, smem_u32(st + row * 128 + ((lchunk ^ (row & 7)) << 4)));
 #pragma unroll
-                for (int mb = 0; mb < 2; ++mb) {
-                    const int o = kk - mb;
-                    if (o >= 0 && o <= 2 * A) {
-                        mma16816<T>(acc[mb][0], af[o], b[0], b[1]);
-                        mma16816<T>(acc[mb][1], af[o], b[2], b[3]);
-                    }
+            for (int mb = 0; mb < 2; ++mb) {
+                const int o = kk - mb;
+                if (o >= 0 && o <= 2 * A) {
+                    mma16816<T>(acc[mb][0], af[o], b[0], b[1]);
+                    mma16816<T>(acc[mb][1], af[o], b[2], b[3]);
                 }
             }
-#pragma unroll
-            for (int mb = 0; mb < 2; ++mb)
-#pragma unroll
-                for (int h = 0; h < 2; ++h)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) px[mb][h][e].step(p, m, acc[mb][h][e]);
         }
-        __syncthreads();                            // stage s fully consumed
-        if (tid == 0 && ok && i + S < C) issue(m - S, s);
-    }
-    if (!ok) {
-        // a load did not land in time: wait (bounded again) for the loads still in flight
-        for (int j = i_fail; j < C && j < i_fail + S; ++j) mbar_wait(&bars[j % S], (unsigned)((j / S) & 1));
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);        // this warp is done with stage s
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) px[mb][h][e].step(p, m, acc[mb][h][e]);
     }
 
     // ---- ratio and store
@@ -383,52 +280,47 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
+size_t kb_smem_bytes(const TcGeom& g) {
+    return (size_t)g.kb_stages * kb_stage_bytes(g.a) + 2 * g.kb_stages * 8 + (16 * (g.a + 1) + 1) * 4 + 1024;
+}
+
 template <typename T, int A>
-cudaError_t launch_tc_impl(const float* f, void* Yv, float* out, const GcParams& p, const Taps& t,
-                           const TcGeom& g, DiagHeader* diag, cudaStream_t s, int which) {
-    T* Y = static_cast<T*>(Yv);
-    if (which == 0) {
-        const size_t smem = (size_t)((g.ka_rows * p.C + 15) & ~15) * ka_pitch_bytes(A);
-        auto kern = k_build_hpass_tc<T, A>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        dim3 grid((g.Wp + KA_COLS - 1) / KA_COLS, (g.Hp + g.ka_rows - 1) / g.ka_rows);
-        kern<<<grid, 256, smem, s>>>(f, Y, p, t, g);
-        return cudaGetLastError();
-    }
+cudaError_t launch_vpass_impl(const float* f, void* Yv, float* out, const GcParams& p, const Taps& t,
+                              const TcGeom& g, DiagHeader* diag, cudaStream_t s) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
+    // Y[p][c][x] as a 3-D tensor: x (Wp), c (C), p (Hp); one box = 64 columns x 1 channel x rows
     alignas(64) CUtensorMap map;
-    const cuuint64_t dims[2] = {(cuuint64_t)g.Wp, (cuuint64_t)p.C * g.Hp};
-    const cuuint64_t strides[1] = {(cuuint64_t)g.Wp * sizeof(T)};
-    const cuuint32_t box[2] = {(cuuint32_t)KB_COLS, (cuuint32_t)g.kb_box_rows};
-    const cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(&map, sizeof(T) == 2 && std::is_same<T, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                                                            : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
-                     2, Yv, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+    const cuuint64_t dims[3] = {(cuuint64_t)g.Wp, (cuuint64_t)p.C, (cuuint64_t)g.Hp};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.Wp * sizeof(T), (cuuint64_t)p.C * g.Wp * sizeof(T)};
+    const cuuint32_t box[3] = {(cuuint32_t)KB_COLS, 1u, (cuuint32_t)g.kb_box_rows};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(&map, std::is_same<T, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                          : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                     3, Yv, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)g.kb_stages * kb_stage_bytes(A) + 64 * 8 + 1024;
+    const size_t smem = kb_smem_bytes(g);
     auto kern = k_vpass_combine_tc<T, A>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((g.Wp + KB_COLS - 1) / KB_COLS, (g.Hp - 2 * g.P) / KB_ROWS);
-    kern<<<grid, 256, smem, s>>>(map, f, out, p, t, g, diag);
+    kern<<<grid, 32 * (KB_CONSUMERS + 1), smem, s>>>(map, f, out, p, t, g, diag);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_tc_a(const float* f, void* Y, float* out, const GcParams& p, const Taps& t, const TcGeom& g,
-                        DiagHeader* diag, cudaStream_t s, int which) {
+cudaError_t launch_vpass_a(const float* f, void* Y, float* out, const GcParams& p, const Taps& t, const TcGeom& g,
+                           DiagHeader* diag, cudaStream_t s) {
     switch (g.a) {
-    case 1: return launch_tc_impl<T, 1>(f, Y, out, p, t, g, diag, s, which);
-    case 2: return launch_tc_impl<T, 2>(f, Y, out, p, t, g, diag, s, which);
-    case 3: return launch_tc_impl<T, 3>(f, Y, out, p, t, g, diag, s, which);
-    case 4: return launch_tc_impl<T, 4>(f, Y, out, p, t, g, diag, s, which);
-    case 5: return launch_tc_impl<T, 5>(f, Y, out, p, t, g, diag, s, which);
-    case 6: return launch_tc_impl<T, 6>(f, Y, out, p, t, g, diag, s, which);
-    case 7: return launch_tc_impl<T, 7>(f, Y, out, p, t, g, diag, s, which);
-    case 8: return launch_tc_impl<T, 8>(f, Y, out, p, t, g, diag, s, which);
+    case 1: return launch_vpass_impl<T, 1>(f, Y, out, p, t, g, diag, s);
+    case 2: return launch_vpass_impl<T, 2>(f, Y, out, p, t, g, diag, s);
+    case 3: return launch_vpass_impl<T, 3>(f, Y, out, p, t, g, diag, s);
+    case 4: return launch_vpass_impl<T, 4>(f, Y, out, p, t, g, diag, s);
+    case 5: return launch_vpass_impl<T, 5>(f, Y, out, p, t, g, diag, s);
+    case 6: return launch_vpass_impl<T, 6>(f, Y, out, p, t, g, diag, s);
+    case 7: return launch_vpass_impl<T, 7>(f, Y, out, p, t, g, diag, s);
+    case 8: return launch_vpass_impl<T, 8>(f, Y, out, p, t, g, diag, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -442,36 +334,32 @@ TcGeom tc_geometry(int H, int W, int R, int C) {
     g.P = 16 * g.a;
     g.Hp = (H + KB_ROWS - 1) / KB_ROWS * KB_ROWS + 2 * g.P;
     g.Wp = (W + KB_COLS - 1) / KB_COLS * KB_COLS;
-    // kernel A: padded rows per tile, as many as fit ~100 KB of channel rows (at most 4)
-    const int pitch = ka_pitch_bytes(g.a);
-    g.ka_rows = 4;
-    while (g.ka_rows > 1 && (size_t)((g.ka_rows * C + 15) & ~15) * pitch > 100 * 1024) --g.ka_rows;
-    // kernel B: TMA box of at most 256 rows; stages that fit ~150 KB
+    // column pass: TMA box of at most 256 rows; stages that fit ~150 KB
     const int rows = kb_tile_rows(g.a);
     g.kb_box_rows = rows <= 256 ? rows : rows / 2;
     g.kb_stages = 4;
     while (g.kb_stages > 2 && (size_t)g.kb_stages * kb_stage_bytes(g.a) > 150 * 1024) --g.kb_stages;
+    // tcgen05 row pass
+    g.u_tw = g.a <= 4 ? 256 : 64;
+    g.u_rows = std::max(1, std::min(128 / std::max(1, C), umma_max_octets() / ((g.u_tw + 32 * g.a) / 8)));
+    g.u_hb = (g.a + 3) / 4;
+    g.u_nkb = g.u_tw / 64 + 2 * g.u_hb;
+    g.u_kbb = (64 + 32 * g.a + 63) / 64;
     return g;
 }
 
 size_t tc_workspace_bytes(const TcGeom& g, int C) { return (size_t)C * g.Hp * g.Wp * 2; }
 
 bool tc_supported(int R, int C) {
-    if (R > 16 * BF_TC_MAX_A) return false;
+    if (R > 16 * BF_TC_MAX_A || C > 128) return false;
     const TcGeom g = tc_geometry(64, 64, R, C);
-    return (size_t)((g.ka_rows * C + 15) & ~15) * ka_pitch_bytes(g.a) <= 200 * 1024;
-}
-
-cudaError_t launch_build_hpass_tc(const float* f, void* Y, const GcParams& p, const Taps& t, const TcGeom& g,
-                                  bool fp16, cudaStream_t s) {
-    return fp16 ? launch_tc_a<__half>(f, Y, nullptr, p, t, g, nullptr, s, 0)
-                : launch_tc_a<__nv_bfloat16>(f, Y, nullptr, p, t, g, nullptr, s, 0);
+    return umma_smem_bytes(g) <= 227 * 1024 && kb_smem_bytes(g) <= 227 * 1024;
 }
 
 cudaError_t launch_vpass_combine_tc(const float* f, void* Y, float* out, const GcParams& p, const Taps& t,
                                     const TcGeom& g, bool fp16, DiagHeader* diag, cudaStream_t s) {
-    return fp16 ? launch_tc_a<__half>(f, Y, out, p, t, g, diag, s, 1)
-                : launch_tc_a<__nv_bfloat16>(f, Y, out, p, t, g, diag, s, 1);
+    return fp16 ? launch_vpass_a<__half>(f, Y, out, p, t, g, diag, s)
+                : launch_vpass_a<__nv_bfloat16>(f, Y, out, p, t, g, diag, s);
 }
 
 }  // namespace bfgc
