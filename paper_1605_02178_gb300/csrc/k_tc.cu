@@ -4,26 +4,34 @@
 // GEMM view, per tile of 128 output rows x 64 output columns and per channel m:
 //   D[i][x] = sum_k A[i][k] Y_m[y0 + k][x0 + x],   k = 0 .. 128 + 2P - 1  (P = 16a),
 //   A[i][k] = g(k - P - i), zero where |k - P - i| > R: the banded Toeplitz matrix of the
-//     column Gaussian, 128 x (128 + 32a), K-major with the 128-byte swizzle, built once per
-//     CTA in shared memory;
+//     column Gaussian, 128 x (128 + 32a), held in TENSOR memory for the whole kernel (lane i
+//     = row i, 32-bit column c = elements 2c, 2c + 1), so that the MMAs read only B from
+//     shared memory;
 //   B = the channel's (128 + 32a) x 64 tile of the row-filtered buffer Y, brought in by TMA
 //     with the 128-byte swizzle: each 128-byte line holds the 64 columns of one input row,
 //     i.e. an MN-major operand (8-row groups 1024 bytes apart);
-//   D = 128 tensor-memory lanes x 64 fp32 columns, one of kTBuf accumulator buffers.
+//   D = 128 tensor-memory lanes x 64 fp32 columns, one of NB accumulator buffers in the
+//     tensor-memory columns left over by A.
 // 8 + 2a MMAs of 128 x 64 x 16 per tile and channel: 128 + 32a multiply-adds per output,
-// against 2R + 1 in the direct sum; the tensor cores have the headroom, the kernel is meant
-// to be bound by the HBM read of Y.
+// against 2R + 1 in the direct sum.  With A in tensor memory an MMA moves 2 KB out of shared
+// memory instead of 6 KB (the operand bandwidth of shared memory, 128 bytes per clock, would
+// otherwise cost 48 clocks per MMA against 32 of tensor work).
 //
-// Schedule (persistent CTA, one per SM; tiles ordered so that vertically adjacent tiles,
-// which share 2P halo rows, run at the same time and meet in L2).  A CTA walks its channel
-// steps gi = (tile, channel) in order.  All 16 warps run the ratio epilogue, one thread per
-// output row and 16 columns: per step one tcgen05.ld of 16 accumulators, then the Horner
-// steps of P, Q and the guard scale; at the end of a tile the guarded ratio and the
-// un-centring.  The producer and issuer work rotates over the warps: at step gi, one lane
-// of warp gi mod 16 issues the MMAs of step gi + LA (committed both to the stage's empty
-// barrier and to the accumulator buffer's full barrier) and the TMA load that refills the
-// stage freed by the MMAs of an earlier step.  With no warp set aside for it, each SM
-// sub-partition holds 4 warps and every thread may use 128 registers.
+// Roles (persistent CTA, one per SM; tiles ordered so that vertically adjacent tiles, which
+// share 2P halo rows, run at the same time and meet in L2):
+//   warp 16, one lane : TMA producer over an S-stage ring (full / empty mbarriers);
+//   warps 17, 18, one lane each : MMA issuers of the even and of the odd channel steps; a
+//                       step's MMAs are committed both to the stage's empty barrier (the stage
+//                       may be refilled) and to the accumulator buffer's full barrier (the
+//                       epilogue may read it).  A thread issuing tcgen05.mma is held for about
+//                       45 clocks per 128 x 64 x 16 MMA, so one issuer cannot keep up with the
+//                       epilogue and no epilogue warp issues them;
+//   warps 0 .. 15     : ratio epilogue, one thread per output row and 16 columns: per channel
+//                       one tcgen05.ld of 16 accumulators, then the Horner steps of P, Q and
+//                       the guard scale; at the end of a tile the guarded ratio and the
+//                       un-centring.  The next tile's input pixels are staged in shared
+//                       memory by coalesced cp.async while the current tile runs (registers
+//                       are scarce: 19 warps leave 96 per thread).
 // Every mbarrier wait is bounded; a wait that runs out flags the workspace and raises a
 // shared abort flag that ends the other roles' waits, so the kernel always returns.
 //
@@ -46,10 +54,8 @@ namespace {
 
 constexpr int VR = 128;                          // output rows per tile (tensor-memory lanes)
 constexpr int VC = 64;                           // output columns per tile (MMA N)
-constexpr int kVWarps = 16;                      // 4 per tensor-memory lane quarter (128 registers)
-constexpr int kVThreads = 32 * kVWarps;
-constexpr int kTBuf = 8;                         // accumulator buffers of 64 columns (all 512)
-constexpr int kLA = 4;                           // MMAs issued up to this many channel steps ahead
+constexpr int kEpiWarps = 16;                    // 4 per tensor-memory lane quarter
+constexpr int kVThreads = 32 * (kEpiWarps + 3);
 constexpr unsigned kVSpin = 1u << 22;            // polls per bounded mbarrier wait
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -72,7 +78,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     return ok != 0;
 }
 // Wait for phase `parity` of `bar`.  Gives up when another role raised the abort flag, or
-// (raising it, and flagging the workspace) when the bounded spin runs out.
+// (raising it, and flagging the workspace) when the bounded spin runs out.  (mbarrier waits go
+// by phase parity: every waiter below walks its barrier's phases in order, so the phase before
+// the awaited one is always complete.)
 __device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, unsigned parity, volatile int* abort_flag,
                                                 DiagHeader* diag) {
     for (unsigned i = 0; i < kVSpin; ++i) {
@@ -97,9 +105,8 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
 
 // Shared-memory matrix descriptor with the 128-byte swizzle: start address, leading and
 // stride byte offsets (>> 4), descriptor version 1 (bit 46), swizzle mode 2 (bits 61..63).
-// K-major operand: 8-row groups 1024 bytes apart (SBO), LBO unused.  MN-major operand with
-// 64 elements per line: 8-line (K) groups 1024 bytes apart (SBO), 64-element MN blocks LBO
-// apart (one block here).
+// MN-major operand with 64 elements per line: 8-line (K) groups 1024 bytes apart (SBO),
+// 64-element MN blocks LBO apart (one block here).
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr, uint32_t lbo) {
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFF) >> 4);
@@ -110,14 +117,14 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr, uint32_t lbo) {
     return d;
 }
 
-template <typename T> __device__ __forceinline__ uint16_t to16(float v);
-template <> __device__ __forceinline__ uint16_t to16<__nv_bfloat16>(float v) {
-    __nv_bfloat16 h = __float2bfloat16_rn(v);
-    return *reinterpret_cast<uint16_t*>(&h);
+template <typename T> __device__ __forceinline__ uint32_t pack2(float lo, float hi);
+template <> __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
 }
-template <> __device__ __forceinline__ uint16_t to16<__half>(float v) {
-    __half h = __float2half_rn(v);
-    return *reinterpret_cast<uint16_t*>(&h);
+template <> __device__ __forceinline__ uint32_t pack2<__half>(float lo, float hi) {
+    __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* z) {
@@ -131,17 +138,33 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* z) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) z[j] = __uint_as_float(v[j]);
 }
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* r) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n"
+                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" :: "r"(su32(dst)), "l"(src) : "memory");
+}
 
 }  // namespace
 
-// Input rows of a tile (output rows + halo) and the shared-memory pieces.
+// Input rows of a tile (output rows + halo), tensor-memory columns of A, accumulator buffers
+// (an even number: half for the even channel steps, half for the odd ones).
 __host__ __device__ inline int vu_rows_in(int a) { return VR + 32 * a; }
 __host__ __device__ inline int vu_stage_bytes(int a) { return vu_rows_in(a) * 128; }
-__host__ __device__ inline int vu_a_bytes(int a) { return (vu_rows_in(a) + 63) / 64 * VR * 128; }
+__host__ __device__ inline int vu_a_cols(int a) { return vu_rows_in(a) / 2; }
+__host__ __device__ inline int vu_bufs(int a) { return (512 - vu_a_cols(a)) / VC / 2 * 2; }
+constexpr int kFPitch = VC + 4;                  // floats per row of the staged input tile
+constexpr int kFBytes = VR * kFPitch * 4;
 
-// Shared layout (1024-byte aligned): Toeplitz A | S stages | full[S] | empty[S] | tfull[kTBuf] |
-// tempty[kTBuf] | TMEM slot | abort flag | last channel loaded per stage [S] | last channel
-// committed per accumulator buffer [kTBuf].
+// Shared layout (1024-byte aligned): S stages | f tile [128][68] | full[S] | empty[S] |
+// tfull[NB] | tempty[NB] | TMEM slot | abort flag | last step loaded per stage [S] | last step
+// committed per accumulator buffer [NB].
+// Channel step j uses stage (j & 1) S/2 + (j >> 1) mod S/2 and accumulator buffer
+// (j & 1) NB/2 + (j >> 1) mod NB/2: even and odd steps have their own stages and buffers, so
+// each of the two MMA issuers walks the phases of its barriers in order.
 template <typename T, int A_>
 __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
     const __grid_constant__ CUtensorMap ymap, const float* __restrict__ f, float* __restrict__ out, const GcParams p,
@@ -149,17 +172,17 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
     constexpr int RIN = VR + 32 * A_, KS = RIN / 16, SB = RIN * 128;
-    constexpr int KA = (RIN + 63) / 64;                 // 64-column K-blocks of A
+    constexpr int ACOLS = RIN / 2, NB = (512 - ACOLS) / VC / 2 * 2, NB2 = NB / 2;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int S = g.kb_stages, C = p.C, P = g.P;
+    const int S = g.kb_stages, S2 = S / 2, C = p.C, P = g.P;
     const int box_rows = g.kb_box_rows, loads = RIN / box_rows;
-    unsigned char* As = smem;
-    unsigned char* stages = smem + KA * VR * 128;
-    uint64_t* full = reinterpret_cast<uint64_t*>(stages + (size_t)S * SB);
+    unsigned char* stages = smem;
+    float* fs = reinterpret_cast<float*>(smem + (size_t)S * SB);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * SB + kFBytes);
     uint64_t* empty = full + S;
     uint64_t* tfull = empty + S;
-    uint64_t* tempty = tfull + kTBuf;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + kTBuf);
+    uint64_t* tempty = tfull + NB;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + NB);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     volatile int* stage_k = abort_flag + 1;
     volatile int* buf_j = stage_k + S;
@@ -167,16 +190,11 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
     const int ntiles = tiles_x * tiles_y, G = gridDim.x;
     const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;
     const int total = my_tiles * C;                     // channel steps of this CTA
-    // The MMAs of step gi + LA are issued at step gi, the TMA load of step k once the MMAs of
-    // step k - S (issued TD steps earlier) are done.  mbarrier waits go by phase parity, so a
-    // wait for phase n of a barrier may only start once phase n - 1 is known to be complete:
-    // the issuing warp has consumed every step before gi, hence LA < S (full barriers) and
-    // LA - TD < S (empty barriers).
-    const int LA = S - 1 < kLA ? S - 1 : kLA;
-    const int TD = S >= 3 ? 2 : 1;
+    auto stage_of = [&](int j) { return (j & 1) * S2 + (j >> 1) % S2; };
+    auto buf_of = [&](int j) { return (j & 1) * NB2 + (j >> 1) % NB2; };
 
-    // ---- set-up: TMEM, barriers, the Toeplitz operand
-    if (warp == 0) {
+    // ---- set-up: TMEM, barriers
+    if (warp == kEpiWarps) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" :: "r"(su32(tslot)), "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
@@ -186,156 +204,143 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
             mbar_init(&empty[s], 1);
             stage_k[s] = -1;
         }
-        for (int b = 0; b < kTBuf; ++b) {
+        for (int b = 0; b < NB; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], kVWarps);
+            mbar_init(&tempty[b], kEpiWarps);
             buf_j[b] = -1;
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    for (int idx = tid; idx < VR * KA * 64; idx += blockDim.x) {
-        const int i = idx / (KA * 64), k = idx - i * (KA * 64);
-        const int d = k - P - i, ad = d < 0 ? -d : d;
-        const int kb = k >> 6, kk = k & 63;
-        const uint32_t off = (uint32_t)(kb * VR * 128 + (i >> 3) * 1024 + (i & 7) * 128 +
-                                        (((kk >> 3) ^ (i & 7)) << 4) + (kk & 7) * 2);
-        *reinterpret_cast<uint16_t*>(As + off) = to16<T>(k < RIN && ad <= t.R ? t.g[ad] : 0.0f);
-    }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tbase = *tslot;
+    const uint32_t tacc = tbase + (uint32_t)(512 - NB * VC);         // accumulator buffers
 
-    // ---- producer / issuer steps (one lane; any warp may run them)
-    // TMA load of channel step k: channel C-1-i of the CTA's tile k / C, padded rows y0 .. y0 + RIN
-    auto issue_tma = [&](int k) {
-        const int it = k / C, i = k - it * C;
-        const int tile = (int)blockIdx.x + it * G;
-        const int x0 = (tile / tiles_y) * VC, y0 = (tile % tiles_y) * VR;
-        const int s = k % S;
-        stage_k[s] = k;
-        mbar_expect_tx(&full[s], (unsigned)SB);
-        for (int l = 0; l < loads; ++l)
-            tma_load_3d(stages + (size_t)s * SB + (size_t)l * box_rows * 128, &ymap, x0, C - 1 - i, y0 + l * box_rows,
-                        &full[s]);
-    };
-    // D f32 (bit 4); A, B f16 (0) or bf16 (1) at bits 7, 10; A K-major (bit 15 = 0), B MN-major
-    // (bit 16 = 1); N / 8 at bit 17, M / 16 at bit 24
-    const uint32_t fmt = std::is_same<T, __half>::value ? 0u : 1u;
-    const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (1u << 16) | ((uint32_t)(VC >> 3) << 17) |
-                           ((uint32_t)(VR >> 4) << 24);
-    // MMAs of channel step j: stage j % S against the Toeplitz operand into buffer j % kTBuf
-    auto issue_mma = [&](int j) -> bool {
-        const int s = j % S, b = j % kTBuf;
-        if (!mbar_wait_abort(&full[s], (unsigned)((j / S) & 1), abort_flag, diag)) return false;
-        if (j >= kTBuf && !mbar_wait_abort(&tempty[b], (unsigned)(((j / kTBuf) - 1) & 1), abort_flag, diag))
-            return false;
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const uint64_t a0 = sw128_desc(su32(As), 16);
-        const uint64_t b0 = sw128_desc(su32(stages + (size_t)s * SB), SB);
-        const uint32_t d = tbase + (uint32_t)(b * VC);
-#pragma unroll
-        for (int ks = 0; ks < KS; ++ks) {
-            // descriptors advance by adding (byte offset >> 4) to the start address
-            const uint64_t ad = a0 + (uint64_t)(((uint32_t)(ks >> 2) * VR * 128u + (uint32_t)(ks & 3) * 32u) >> 4);
-            const uint64_t bd = b0 + (uint64_t)(((uint32_t)ks * 16u * 128u) >> 4);
-            asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
-                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n"
-                         :: "r"(d), "l"(ad), "l"(bd), "r"(idesc), "r"(ks > 0 ? 1u : 0u));
-        }
-        buf_j[b] = j;
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                     :: "r"(su32(&empty[s])) : "memory");
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                     :: "r"(su32(&tfull[b])) : "memory");
-        return true;
-    };
-    // the MMAs of channel step c have completed (its stage may be refilled)
-    auto mma_done = [&](int c) -> bool {
-        return mbar_wait_abort(&empty[c % S], (unsigned)((c / S) & 1), abort_flag, diag);
-    };
-    // Work of step gi: the MMAs of step gi + LA and the load of step gi + LA + S - TD.  Every
-    // wait is on work of an earlier step, so the round-robin over warps cannot deadlock.
-    auto control = [&](int gi) -> bool {
-        const int j = gi + LA;
-        if (j < total && !issue_mma(j)) return false;
-        const int k = j + S - TD;
-        if (k < total) {
-            if (!mma_done(k - S)) return false;
-            issue_tma(k);
-        }
-        return true;
-    };
-
-    // ---- prologue (one thread): the loads of steps 0 .. LA + S - TD - 1 and the MMAs of
-    // steps 0 .. LA - 1, each MMA after its load (a load past the ring waits for the MMAs of
-    // the step that last used its stage)
-    if (tid == 0) {
-        bool ok = true;
-        int next_k = 0;
-        auto load_upto = [&](int last) {
-            for (; ok && next_k <= last && next_k < total; ++next_k) {
-                if (next_k >= S && !(ok = mma_done(next_k - S))) break;
-                issue_tma(next_k);
-            }
+    // ---- the Toeplitz operand into tensor memory: warp q < 4 writes lanes 32q .. 32q + 31
+    if (warp < 4) {
+        const int i = 32 * warp + lane;
+        auto tap = [&](int k) {
+            const int d = k - P - i, ad = d < 0 ? -d : d;
+            return ad <= t.R ? t.g[ad] : 0.0f;
         };
-        load_upto(S - 1);
-        for (int j = 0; j < LA && j < total && ok; ++j) {
-            load_upto(j);
-            if (ok) ok = issue_mma(j);
+        for (int c0 = 0; c0 < ACOLS; c0 += 8) {
+            uint32_t r[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) r[e] = pack2<T>(tap(2 * (c0 + e)), tap(2 * (c0 + e) + 1));
+            tmem_st8(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, r);
         }
-        load_upto(LA + S - TD - 1);
+        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
     }
-    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 
-    // ---- ratio epilogue (every warp), one thread per output row and 16 columns
-    {
+    if (warp == kEpiWarps) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            for (int k = 0; k < total; ++k) {
+                const int it = k / C, i = k - it * C, s = stage_of(k), use = (k >> 1) / S2;
+                const int tile = (int)blockIdx.x + it * G;
+                const int x0 = (tile / tiles_y) * VC, y0 = (tile % tiles_y) * VR;
+                if (use > 0 && !mbar_wait_abort(&empty[s], (unsigned)((use - 1) & 1), abort_flag, diag)) break;
+                stage_k[s] = k;
+                mbar_expect_tx(&full[s], (unsigned)SB);
+                // padded rows y0 .. y0 + RIN of channel C-1-i (highest channel first)
+                for (int l = 0; l < loads; ++l)
+                    tma_load_3d(stages + (size_t)s * SB + (size_t)l * box_rows * 128, &ymap, x0, C - 1 - i,
+                                y0 + l * box_rows, &full[s]);
+            }
+        }
+    } else if (warp > kEpiWarps) {
+        // ------------------------------------------------------------ MMA issuers (even, odd steps)
+        if (lane == 0) {
+            // D f32 (bit 4); A, B f16 (0) or bf16 (1) at bits 7, 10; A K-major (bit 15 = 0),
+            // B MN-major (bit 16 = 1); N / 8 at bit 17, M / 16 at bit 24
+            const uint32_t fmt = std::is_same<T, __half>::value ? 0u : 1u;
+            const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (1u << 16) | ((uint32_t)(VC >> 3) << 17) |
+                                   ((uint32_t)(VR >> 4) << 24);
+            for (int j = warp - kEpiWarps - 1; j < total; j += 2) {
+                const int s = stage_of(j), b = buf_of(j);
+                const int suse = (j >> 1) / S2, buse = (j >> 1) / NB2;
+                if (!mbar_wait_abort(&full[s], (unsigned)(suse & 1), abort_flag, diag)) break;
+                if (buse > 0 && !mbar_wait_abort(&tempty[b], (unsigned)((buse - 1) & 1), abort_flag, diag)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint64_t b0 = sw128_desc(su32(stages + (size_t)s * SB), SB);
+                const uint32_t d = tacc + (uint32_t)(b * VC);
+#pragma unroll
+                for (int ks = 0; ks < KS; ++ks) {
+                    // A: 8 tensor-memory columns per k-step; B: 16 lines of 128 bytes per k-step
+                    const uint64_t bd = b0 + (uint64_t)(((uint32_t)ks * 16u * 128u) >> 4);
+                    asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+                                 " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, q;\n}\n"
+                                 :: "r"(d), "r"(tbase + (uint32_t)(8 * ks)), "l"(bd), "r"(idesc),
+                                    "r"(ks > 0 ? 1u : 0u));
+                }
+                buf_j[b] = j;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                             :: "r"(su32(&empty[s])) : "memory");
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                             :: "r"(su32(&tfull[b])) : "memory");
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ ratio epilogue
         const int q = warp & 3, cg = warp >> 2;
         const int row = 32 * q + lane;                     // tile-local output row = TMEM lane
-        const uint32_t tl = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * cg);
+        const uint32_t tl = tacc + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * cg);
         const bool vec = (p.W & 3) == 0;
         unsigned guarded = 0, f64 = 0;
         bool ok = true;
-        float fv[16];
-        auto load_f = [&](int tile) {
-            const int y = (tile % tiles_y) * VR + row, xb = (tile / tiles_y) * VC + 16 * cg;
+        // the tile's 128 x 64 input pixels into fs, 16 bytes per copy, consecutive threads on
+        // consecutive addresses (t_c outside the image)
+        auto fetch_f = [&](int tile) {
+            if (tile >= ntiles) return;
+            const int y0 = (tile % tiles_y) * VR, x0 = (tile / tiles_y) * VC;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) fv[j] = p.t_c;
-            if (tile < ntiles && y < p.H) {
-                const float* fr = f + (size_t)y * p.W;
-                if (vec && xb + 16 <= p.W) {
-#pragma unroll
-                    for (int j = 0; j < 16; j += 4) {
-                        const float4 v = __ldg(reinterpret_cast<const float4*>(fr + xb + j));
-                        fv[j] = v.x; fv[j + 1] = v.y; fv[j + 2] = v.z; fv[j + 3] = v.w;
-                    }
+            for (int k = 0; k < 4; ++k) {
+                const int c = tid + 512 * k, r = c >> 4, x = x0 + 4 * (c & 15), y = y0 + r;
+                float* dst = fs + r * kFPitch + 4 * (c & 15);
+                const float* src = f + (size_t)y * p.W + x;
+                if (vec && y < p.H && x + 4 <= p.W) {
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" :: "r"(su32(dst)), "l"(src) : "memory");
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (xb + j < p.W) fv[j] = __ldg(fr + xb + j);
+                    for (int e = 0; e < 4; ++e) {
+                        if (y < p.H && x + e < p.W) cp_async4(dst + e, src + e);
+                        else dst[e] = p.t_c;
+                    }
                 }
             }
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
         };
-        load_f(blockIdx.x);
+        auto epi_sync = [] { asm volatile("bar.sync 1, 512;\n" ::: "memory"); };
+        fetch_f(blockIdx.x);
         int gi = 0;
-        for (int it = 0; it < my_tiles && ok; ++it) {
+        for (int it = 0; it < my_tiles; ++it) {
             const int tile = (int)blockIdx.x + it * G;
             const int y = (tile % tiles_y) * VR + row, xb = (tile / tiles_y) * VC + 16 * cg;
             float u[16], P_[16], Q_[16], Qa[16];
+            // this tile's pixels (every warp passes both barriers, also after an abort)
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+            epi_sync();
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float4 v = *reinterpret_cast<const float4*>(fs + row * kFPitch + 16 * cg + 4 * k);
+                u[4 * k] = v.x; u[4 * k + 1] = v.y; u[4 * k + 2] = v.z; u[4 * k + 3] = v.w;
+            }
+            epi_sync();
+            fetch_f(tile + G);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                u[j] = (fv[j] - p.t_c) * p.inv_sr;
+                u[j] = (u[j] - p.t_c) * p.inv_sr;
                 P_[j] = Q_[j] = Qa[j] = 0.0f;
             }
-            for (int i = 0; i < C; ++i, ++gi) {
-                const int b = gi % kTBuf, m = C - 1 - i;
+            for (int i = 0; i < C && ok; ++i, ++gi) {
+                const int b = buf_of(gi), m = C - 1 - i;
                 bool w = true;
-                if (lane == 0) {
-                    if ((gi & (kVWarps - 1)) == warp) w = control(gi);
-                    w = w && mbar_wait_abort(&tfull[b], (unsigned)((gi / kTBuf) & 1), abort_flag, diag);
-                }
+                if (lane == 0) w = mbar_wait_abort(&tfull[b], (unsigned)(((gi >> 1) / NB2) & 1), abort_flag, diag);
                 ok = __shfl_sync(0xffffffffu, w, 0);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -360,10 +365,9 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
                     }
                 }
             }
-            if (!ok) break;
-            if (it + 1 < my_tiles) load_f(tile + G);        // next tile's pixels, in flight meanwhile
             // eq. (10) with the division guard (see RatioAcc::finish), then the store
-            if (y < p.H) {
+            if (ok && y < p.H) {
+                float* orow = out + (size_t)y * p.W;
                 float o[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -377,7 +381,6 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
                         o[j] = p.s_r * P_[j] / Q_[j] + p.t_c;
                     }
                 }
-                float* orow = out + (size_t)y * p.W;
                 if (vec && xb + 16 <= p.W) {
 #pragma unroll
                     for (int j = 0; j < 16; j += 4)
@@ -389,6 +392,7 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
                 }
             }
         }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
         count_diag(diag, guarded, f64);
     }
 
@@ -398,12 +402,12 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
     __syncthreads();
     if (tid == 0) {
         for (int s = 0; s < S; ++s)
-            if (stage_k[s] >= 0) mbar_drain(&full[s], (unsigned)((stage_k[s] / S) & 1));
-        for (int b = 0; b < kTBuf; ++b)
-            if (buf_j[b] >= 0) mbar_drain(&tfull[b], (unsigned)((buf_j[b] / kTBuf) & 1));
+            if (stage_k[s] >= 0) mbar_drain(&full[s], (unsigned)(((stage_k[s] >> 1) / S2) & 1));
+        for (int b = 0; b < NB; ++b)
+            if (buf_j[b] >= 0) mbar_drain(&tfull[b], (unsigned)(((buf_j[b] >> 1) / NB2) & 1));
     }
     __syncthreads();
-    if (warp == 0) {
+    if (warp == kEpiWarps) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tbase), "r"(512));
     }
@@ -430,8 +434,9 @@ EncodeTiledFn encode_fn() {
 }
 
 size_t vu_smem_bytes(const TcGeom& g) {
-    return (size_t)vu_a_bytes(g.a) + (size_t)g.kb_stages * vu_stage_bytes(g.a) + (2 * g.kb_stages + 2 * kTBuf) * 8 +
-           8 + 4 * (g.kb_stages + kTBuf) + 1024;
+    const int nb = vu_bufs(g.a);
+    return (size_t)g.kb_stages * vu_stage_bytes(g.a) + kFBytes + (2 * g.kb_stages + 2 * nb) * 8 + 8 +
+           4 * (g.kb_stages + nb) + 1024;
 }
 
 template <typename T, int A>
@@ -488,13 +493,13 @@ TcGeom tc_geometry(int H, int W, int R, int C) {
     g.P = 16 * g.a;
     g.Hp = (H + VR - 1) / VR * VR + 2 * g.P;
     g.Wp = (W + VC - 1) / VC * VC;
-    // column pass: TMA boxes of at most 256 rows; as many ring stages (<= 8) as fit beside
-    // the Toeplitz operand in ~200 KB
+    // column pass: TMA boxes of at most 256 rows; an even number of ring stages (<= 8, half
+    // for the even channel steps, half for the odd ones) beside the staged input tile in ~205 KB
     const int rows = vu_rows_in(g.a);
     g.kb_box_rows = rows <= 256 ? rows : rows / 2;
     g.kb_stages = 8;
-    while (g.kb_stages > 2 && (size_t)vu_a_bytes(g.a) + (size_t)g.kb_stages * vu_stage_bytes(g.a) > 200 * 1024)
-        --g.kb_stages;
+    while (g.kb_stages > 2 && (size_t)kFBytes + (size_t)g.kb_stages * vu_stage_bytes(g.a) > 205 * 1024)
+        g.kb_stages -= 2;
     // tcgen05 row pass
     g.u_tw = g.a <= 4 ? 256 : 64;
     g.u_rows = std::max(1, std::min(128 / std::max(1, C), umma_max_octets() / ((g.u_tw + 32 * g.a) / 8)));
@@ -509,7 +514,7 @@ size_t tc_workspace_bytes(const TcGeom& g, int C) { return (size_t)C * g.Hp * g.
 bool tc_supported(int R, int C) {
     if (R > 16 * BF_TC_MAX_A || C > 128) return false;
     const TcGeom g = tc_geometry(64, 64, R, C);
-    return umma_smem_bytes(g) <= 227 * 1024 && vu_smem_bytes(g) <= 227 * 1024;
+    return umma_smem_bytes(g) <= 227 * 1024 && vu_smem_bytes(g) <= 227 * 1024 && vu_bufs(g.a) >= 2;
 }
 
 cudaError_t launch_vpass_combine_tc(const float* f, void* Y, float* out, const GcParams& p, const Taps& t,
