@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--forms", default=None, help="comma list of form:precision to run")
     ap.add_argument("--size", default=None, help="HxW instead of 2160x3840 (profiling cases)")
+    ap.add_argument("--study", default=None, choices=["precision", "gpf"],
+                    help="instead of the benchmark: the 8192x8192 precision sweep, or the GPF/GCF table at 4K")
     args = ap.parse_args()
     if args.size:
         global H, W
@@ -374,9 +376,75 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+# --------------------------------------------------------------------------- studies
+def run_study(args):
+    """One JSON line per result.  `precision`: 8192x8192 edge+smooth image (seed 5),
+    sigma_s in {8, 16, 32}, sigma_r = 30, N in {12, 28}; BF16 / FP16 channel storage (fused
+    tensor-core form) and FP32 (plain): ms per image (CUDA events, 5 runs after 2 warm-ups),
+    max-abs against the FP64 oracle at 52 sampled pixels, PSNR against the exact filter
+    (bf_direct).  `gpf`: the 4K benchmark image at sigma_s = 5, sigma_r = 30, MSE (dB) of the
+    Gauss-polynomial and Gauss-Chebyshev filters (plain FP32) against the exact filter for the
+    degrees of Table 1."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1605_02178_gb300 import api, bfgc, synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    if args.study == "gpf":
+        f = synth.workload("uhd")["f"]
+        ft = torch.from_numpy(f).to(dev)
+        ex = bfgc.bf_direct(ft, 5.0, 30.0).cpu().numpy().astype(np.float64)
+        for N in (4, 8, 10, 12, 16, 20, 25):
+            row = {"study": "gpf", "image": "uhd 3840x2160", "sigma_s": 5.0, "sigma_r": 30.0, "N": N}
+            for poly in ("taylor", "chebyshev"):
+                plan = api.GCPlan(2160, 3840, 5.0, 30.0, N, form="plain", poly=poly)
+                out = plan.forward(ft).cpu().numpy().astype(np.float64)
+                row["GPF_mse_db" if poly == "taylor" else "GCF_mse_db"] = oracle.mse_db(out, ex)
+            print(json.dumps(row), flush=True)
+        return
+    f = synth.workload("8k")["f"]
+    H, W = f.shape
+    ft = torch.from_numpy(f).to(dev)
+    rng = np.random.default_rng(7)
+    idx = np.concatenate([[0, W - 1, (H - 1) * W, H * W - 1], rng.integers(0, H * W, 48)])
+    stream = torch.cuda.current_stream(dev)
+    for ss in (8.0, 16.0, 32.0):
+        exact = bfgc.bf_direct(ft, ss, 30.0)
+        torch.cuda.synchronize(dev)
+        exn = exact.cpu().numpy().astype(np.float64)
+        for N in (12, 28):
+            ref = oracle.gcf_at(f, idx, ss, 30.0, N)
+            for form, prec in (("fused_tc", "bf16"), ("fused_tc", "fp16"), ("plain", "fp32")):
+                plan = api.GCPlan(H, W, ss, 30.0, N, form=form, precision=prec)
+                ws = plan.workspace("fwd", dev)
+                out = torch.empty_like(ft)
+                for _ in range(2):
+                    plan.forward(ft, out, ws, stream)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(5):
+                    plan.forward(ft, out, ws, stream)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                o = out.cpu().numpy().astype(np.float64)
+                d = plan.diagnostics(ws, stream)
+                print(json.dumps({
+                    "study": "precision", "image": "8192x8192 edge+smooth (seed 5)", "sigma_s": ss,
+                    "sigma_r": 30.0, "N": N, "form": form, "precision": prec,
+                    "fit_err": plan.info["fit_err"], "ms": e0.elapsed_time(e1) / 5,
+                    "maxabs_vs_fp64_oracle_sampled": float(np.abs(o.reshape(-1)[idx] - ref).max()),
+                    "samples": int(idx.size), "psnr_vs_exact_db": oracle.psnr_db(o, exn),
+                    "n_guarded": d["n_guarded"], "error_flags": d["error_flags"]}), flush=True)
+                del plan, ws, out
+                torch.cuda.empty_cache()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.study:
+        run_study(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

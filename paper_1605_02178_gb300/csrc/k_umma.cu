@@ -58,6 +58,13 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int k, int rows) {
                       (kk & 7) * 2);
 }
 
+// FP16 channels are stored times 2^14: |e u^n| <= 1, so the scaled channels and their
+// Gaussian averages stay below 2^14 (FP16 max 65504), while the high powers of mid-range
+// pixels move out of the FP16 subnormal range.  A power of two is exact, and a common
+// factor of every channel cancels in P/Q and in the relative division guard.
+template <typename T> struct kChannelScale { static constexpr float value = 1.0f; };
+template <> struct kChannelScale<__half> { static constexpr float value = 16384.0f; };
+
 template <typename T> __device__ __forceinline__ uint32_t pack2(float lo, float hi);
 template <> __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -206,7 +213,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_build_hpass_umma(const floa
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 u[e] = (fv[s][e] - p.t_c) * p.inv_sr;
-                v[e] = expf(-p.half_mu * u[e] * u[e]);
+                v[e] = expf(-p.half_mu * u[e] * u[e]) * kChannelScale<T>::value;
             }
             int mrow = r * C;
             for (int c = 0; c < C; ++c, ++mrow) {
