@@ -92,7 +92,8 @@ typedef struct {
 /* Device-side diagnostics written by the last forward into its workspace. */
 typedef struct {
     unsigned long long n_guarded;   /* pixels with |Q| < 1e-12 sum|terms of Q|: output = input */
-    unsigned long long n_fp64_div;  /* pixels divided in FP64 (|Q| < 1e-3 sum|terms of Q|) */
+    unsigned long long n_illcond;   /* pixels with |Q| < 1e-3 sum|terms of Q| (divided like the
+                                       rest, in FP32; a conditioning diagnostic) */
     unsigned int error_flags;       /* bit 0: a bounded wait timed out in a pipelined kernel */
 } bf_gc_diag;
 

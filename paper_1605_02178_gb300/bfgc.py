@@ -37,7 +37,7 @@ class bf_gc_info(ctypes.Structure):
 
 
 class bf_gc_diag(ctypes.Structure):
-    _fields_ = [("n_guarded", ctypes.c_ulonglong), ("n_fp64_div", ctypes.c_ulonglong),
+    _fields_ = [("n_guarded", ctypes.c_ulonglong), ("n_illcond", ctypes.c_ulonglong),
                 ("error_flags", ctypes.c_uint)]
 
 
@@ -179,7 +179,7 @@ def bf_gc_diagnostics(plan, ws, stream=None):
     st = lib().bf_gc_diagnostics(plan, _ptr(ws), ctypes.byref(d), _stream(stream))
     if st not in (BF_OK, BF_ERR_TIMEOUT):
         _check(st, "bf_gc_diagnostics")
-    return {"n_guarded": d.n_guarded, "n_fp64_div": d.n_fp64_div, "error_flags": d.error_flags}
+    return {"n_guarded": d.n_guarded, "n_illcond": d.n_illcond, "error_flags": d.error_flags}
 
 
 def bf_gc_plan_destroy(plan):

@@ -34,31 +34,28 @@ struct RatioAcc {
             Qa = fmaf(Qa, au, fabsf(q));
         }
     }
-    // Eq. (10) with the division guard; *how: 0 = FP32 divide, 1 = FP64 divide
-    // (|Q| < 1e-3 Qa), 2 = guarded (|Q| < 1e-12 Qa, non-finite, or all terms zero):
-    // the input pixel is returned.
+    // Eq. (10) with the division guard; *how: 0 = conditioned, 1 = ill-conditioned
+    // (|Q| < 1e-3 Qa, counted), 2 = guarded (|Q| < 1e-12 Qa, non-finite, or all terms zero):
+    // the input pixel is returned.  The division is FP32 in every case: P and Q are FP32
+    // values, so their FP32 quotient is already correctly rounded.
     __device__ __forceinline__ float finish(const GcParams& p, float f, int* how) const {
         if (!(fabsf(Q) >= 1e-12f * Qa) || !(Qa > 0.0f)) {
             *how = 2;
             return f;
         }
-        if (fabsf(Q) < 1e-3f * Qa) {
-            *how = 1;
-            return (float)((double)p.s_r * (double)P / (double)Q) + p.t_c;
-        }
-        *how = 0;
+        *how = fabsf(Q) < 1e-3f * Qa ? 1 : 0;
         return p.s_r * P / Q + p.t_c;
     }
 };
 
 // Warp-aggregated update of the diagnostics counters.
-__device__ __forceinline__ void count_diag(DiagHeader* diag, unsigned guarded, unsigned f64) {
+__device__ __forceinline__ void count_diag(DiagHeader* diag, unsigned guarded, unsigned illcond) {
     const unsigned mask = __activemask();
     const unsigned g = __reduce_add_sync(mask, guarded);
-    const unsigned d = __reduce_add_sync(mask, f64);
+    const unsigned d = __reduce_add_sync(mask, illcond);
     if ((threadIdx.x & 31) == (unsigned)(__ffs(mask) - 1)) {
         if (g) atomicAdd(&diag->n_guarded, (unsigned long long)g);
-        if (d) atomicAdd(&diag->n_fp64_div, (unsigned long long)d);
+        if (d) atomicAdd(&diag->n_illcond, (unsigned long long)d);
     }
 }
 

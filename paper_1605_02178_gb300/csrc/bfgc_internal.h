@@ -18,7 +18,7 @@
 // Diagnostics header at the start of a workspace.
 struct DiagHeader {
     unsigned long long n_guarded;
-    unsigned long long n_fp64_div;
+    unsigned long long n_illcond;
     unsigned int error_flags;
     unsigned int pad[11];
 };

@@ -243,14 +243,14 @@ __global__ void __launch_bounds__(256) k_combine(const float* __restrict__ f, co
             for (int k = 0; k < 4; ++k) acc[k].step(p, m, z[k]);
         }
         float o[4];
-        unsigned guarded = 0, f64 = 0;
+        unsigned guarded = 0, illcond = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             int how;
             o[k] = acc[k].finish(p, fv[k], &how);
             if (i0 + k < px) {
                 guarded += how == 2;
-                f64 += how == 1;
+                illcond += how == 1;
             }
         }
         if (full) {
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(256) k_combine(const float* __restrict__ f, co
             for (int k = 0; k < 4; ++k)
                 if (i0 + k < px) out[i0 + k] = o[k];
         }
-        count_diag(diag, guarded, f64);
+        count_diag(diag, guarded, illcond);
     }
 }
 

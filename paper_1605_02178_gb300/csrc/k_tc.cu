@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
         const int row = 32 * q + lane;                     // tile-local output row = TMEM lane
         const uint32_t tl = tacc + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * cg);
         const bool vec = (p.W & 3) == 0;
-        unsigned guarded = 0, f64 = 0;
+        unsigned guarded = 0, illcond = 0;
         bool ok = true;
         // the tile's 128 x 64 input pixels into fs, 16 bytes per copy, consecutive threads on
         // consecutive addresses (t_c outside the image)
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
                     }
                 }
             }
-            // eq. (10) with the division guard (see RatioAcc::finish), then the store
+            // eq. (10) with the division guard (see RatioAcc::finish; FP32 division), then the store
             if (ok && y < p.H) {
                 float* orow = out + (size_t)y * p.W;
                 float o[16];
@@ -374,10 +374,8 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
                     if (!(fabsf(Q_[j]) >= 1e-12f * Qa[j]) || !(Qa[j] > 0.0f)) {
                         o[j] = xb + j < p.W ? __ldg(f + (size_t)y * p.W + xb + j) : 0.0f;
                         guarded += xb + j < p.W;
-                    } else if (fabsf(Q_[j]) < 1e-3f * Qa[j]) {
-                        o[j] = (float)((double)p.s_r * (double)P_[j] / (double)Q_[j]) + p.t_c;
-                        f64 += xb + j < p.W;
                     } else {
+                        illcond += xb + j < p.W && fabsf(Q_[j]) < 1e-3f * Qa[j];
                         o[j] = p.s_r * P_[j] / Q_[j] + p.t_c;
                     }
                 }
@@ -393,7 +391,7 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
             }
         }
         asm volatile("cp.async.wait_all;\n" ::: "memory");
-        count_diag(diag, guarded, f64);
+        count_diag(diag, guarded, illcond);
     }
 
     // ---- drain: every load issued has landed and every MMA committed has completed (both

@@ -430,7 +430,7 @@ bf_status bf_gc_diagnostics(bf_gc_plan_t p, const void* ws, bf_gc_diag* out, bf_
     if (cudaMemcpyAsync(&h, ws, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return BF_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return BF_ERR_CUDA;
     out->n_guarded = h.n_guarded;
-    out->n_fp64_div = h.n_fp64_div;
+    out->n_illcond = h.n_illcond;
     out->error_flags = h.error_flags;
     return h.error_flags ? BF_ERR_TIMEOUT : BF_OK;
 }
