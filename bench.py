@@ -43,8 +43,10 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--forms", default=None, help="comma list of form:precision to run")
     ap.add_argument("--size", default=None, help="HxW instead of 2160x3840 (profiling cases)")
-    ap.add_argument("--study", default=None, choices=["precision", "gpf"],
-                    help="instead of the benchmark: the 8192x8192 precision sweep, or the GPF/GCF table at 4K")
+    ap.add_argument("--study", default=None, choices=["precision", "gpf", "batch"],
+                    help="instead of the benchmark: the 8192x8192 precision sweep, the GPF/GCF table at 4K, "
+                         "or the uneven 256-image batch")
+    ap.add_argument("--batch-count", type=int, default=256, help="images of the batch study")
     args = ap.parse_args()
     if args.size:
         global H, W
@@ -391,6 +393,9 @@ def run_study(args):
     from paper_1605_02178_gb300 import api, bfgc, synth
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
+    if args.study == "batch":
+        run_batch_study(args, dev)
+        return
     if args.study == "gpf":
         f = synth.workload("uhd")["f"]
         ft = torch.from_numpy(f).to(dev)
@@ -438,6 +443,87 @@ def run_study(args):
                     "n_guarded": d["n_guarded"], "error_flags": d["error_flags"]}), flush=True)
                 del plan, ws, out
                 torch.cuda.empty_cache()
+
+
+def run_batch_study(args, dev):
+    """The uneven batch (synth.batch_specs(256, seed=4): H, W in 64..2048, own sigma_s, sigma_r
+    and N per image, edge+smooth content).  Times, on one stream with CUDA events (2 warm-ups,
+    3 timed runs, inputs and outputs 2.4 GB >> L2): the per-image loop of the plain FP32
+    kernels, the per-image loop of the tensor-core form (BF16), and the batch graph of the
+    tensor-core form with 1..16 branches and with the autotuned tile widths and branch count.
+    Checks every image of the batch against its per-image forward (bit-exact) and sampled
+    pixels of the convergent images (fit error <= 1e-2) against the oracle."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1605_02178_gb300 import api, autotune, synth
+    from paper_1605_02178_gb300.batch import GCBatch
+    specs = synth.batch_specs(args.batch_count, seed=4)
+    px = sum(s["H"] * s["W"] for s in specs)
+    fs = [torch.from_numpy(synth.edge_smooth_image(s["H"], s["W"], noise_std=5.0, seed=s["seed"])).to(dev)
+          for s in specs]
+    outs = [torch.empty_like(f) for f in fs]
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(run, reps=3, warm=2):
+        for _ in range(warm):
+            run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            run()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    def line(mode, ms, **kw):
+        print(json.dumps({"study": "batch", "images": len(specs), "mpixels": px / 1e6, "mode": mode, "ms": ms,
+                          "mpixel_per_s": px / 1e3 / ms, **kw}), flush=True)
+
+    for form, prec in (("plain", "fp32"), ("fused_tc", "bf16")):
+        plans = [api.GCPlan(s["H"], s["W"], s["sigma_s"], s["sigma_r"], s["N"], form=form, precision=prec)
+                 for s in specs]
+        ws = torch.empty(max(p.workspace_bytes()[0] for p in plans), dtype=torch.uint8, device=dev)
+
+        def loop():
+            for p, f, o in zip(plans, fs, outs):
+                p.forward(f, o, ws, stream)
+        line(f"per-image loop, {form} {prec}", timed(loop), launches_per_batch=len(specs) * (4 if form == "plain" else 2))
+        if form == "fused_tc":
+            ref = [o.clone() for o in outs]
+        del plans, ws
+        torch.cuda.empty_cache()
+    for k in autotune.BRANCH_COUNTS:
+        bt = GCBatch(specs, form="fused_tc", precision="bf16", branches=k)
+        ms = timed(lambda: bt.forward(fs, outs, stream))
+        same = sum(bool(torch.equal(o, r)) for o, r in zip(outs, ref))
+        line(f"batch graph, fused_tc bf16, {k} branches", ms, bit_exact_vs_per_image=f"{same}/{len(specs)}",
+             workspace_mb=bt.ws.numel() / 2 ** 20)
+        del bt
+        torch.cuda.empty_cache()
+    tuner = autotune.Autotuner(reps=2)
+    t0 = time.time()
+    bt = GCBatch(specs, form="fused_tc", precision="bf16", tuner=tuner)
+    bt.forward(fs, outs, stream)
+    torch.cuda.synchronize(dev)
+    tune_s = time.time() - t0
+    ms = timed(lambda: bt.forward(fs, outs, stream))
+    same = sum(bool(torch.equal(o, r)) for o, r in zip(outs, ref))
+    widths = {}
+    for p in bt.plans:
+        widths[str(p.tile_w)] = widths.get(str(p.tile_w), 0) + 1
+    rng = np.random.default_rng(11)
+    worst, checked = 0.0, 0
+    for s, f, o in zip(specs, fs, outs):
+        if api.GCPlan(s["H"], s["W"], s["sigma_s"], s["sigma_r"], s["N"]).info["fit_err"] > 1e-2:
+            continue
+        idx = rng.integers(0, s["H"] * s["W"], 8)
+        r = oracle.gcf_at(f.cpu().numpy(), idx, s["sigma_s"], s["sigma_r"], s["N"])
+        worst = max(worst, float(np.abs(o.cpu().numpy().reshape(-1)[idx] - r).max()))
+        checked += 1
+    line("batch graph, fused_tc bf16, autotuned", ms, branches=bt.branches, tile_w_images=widths,
+         tuning_s=round(tune_s, 1), bit_exact_vs_per_image=f"{same}/{len(specs)}",
+         maxabs_vs_fp64_oracle_sampled=worst, oracle_images=checked, oracle_samples=8 * checked)
 
 
 def main():

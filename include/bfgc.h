@@ -56,8 +56,12 @@ enum {
     BF_OPT_RANGE_L = 3,       /* value: L of the intensity range                   (default 0)     */
     BF_OPT_RANGE_U = 4,       /* value: U of the intensity range                   (default 255)   */
     BF_OPT_POLY = 5,          /* value: BF_POLY_*, choice of c_n                   (default CHEB)  */
-    BF_OPT_SAVE_CHANNELS = 6  /* value: 1 = forward leaves the filtered channels in the workspace
+    BF_OPT_SAVE_CHANNELS = 6, /* value: 1 = forward leaves the filtered channels in the workspace
                                  for bf_gc_backward to reuse; 0 = backward recomputes them      */
+    BF_OPT_TILE_W = 7         /* value: output columns per tile of the tensor-core row pass: 0
+                                 (default: 256 when ceil(R/16) <= 4, else 64), 64, 128 or 256;
+                                 128 and 256 need ceil(R/16) <= 4 (else BF_ERR_UNSUPPORTED).
+                                 The result does not depend on it (same products, same order). */
 };
 enum {
     BF_FORM_PLAIN = 0,        /* 4 kernels: build F_n -> row filter -> column filter -> ratio; FP32 */
@@ -166,6 +170,41 @@ bf_status bf_gc_diagnostics(bf_gc_plan_t plan, const void *d_ws, bf_gc_diag *out
                             bf_stream_t stream);
 
 void bf_gc_plan_destroy(bf_gc_plan_t plan);
+
+/* ---- batches of independent images (a deployment aid; the paper filters one image at a
+ * time).  Each image has its own plan (size, sigma_s, sigma_r, N and options), so a batch
+ * may mix sizes and parameters.  The images are split over `branches` concurrent graph
+ * branches (longest processing time first, by an estimate of each plan's work), each
+ * branch with its own workspace slice, and the whole batch runs as one CUDA graph: small
+ * images leave most SMs idle, and the branches fill them with other images' tiles. */
+typedef struct bf_gc_batch_s *bf_gc_batch_t;
+
+/* Host only, no CUDA call.  `plans` (count entries, 1 <= count <= 65536) are borrowed: they
+ * must outlive the batch and are not modified, except that the first forward marks them
+ * used (bf_gc_plan_set then refuses changes).  1 <= branches <= 64.  Plans with profiling
+ * enabled are refused (BF_ERR_INVALID_ARG). */
+bf_status bf_gc_batch_create(int count, const bf_gc_plan_t *plans, int branches, bf_gc_batch_t *out);
+
+/* Workspace bytes for bf_gc_batch_forward: the sum over branches of the largest forward
+ * workspace among the branch's images (each rounded up to 256 bytes).  Host only. */
+bf_status bf_gc_batch_workspace_size(bf_gc_batch_t batch, size_t *bytes);
+
+/* The branch (0 .. branches-1) of image i in branch_of[i] (count entries, may be NULL) and
+ * the number of CUDA graphs captured so far in *captures (may be NULL).  Host only. */
+bf_status bf_gc_batch_info(bf_gc_batch_t batch, int *branch_of, int *captures);
+
+/* Forward of every image: d_out[i] = B_hat[d_f[i]].  d_f and d_out are HOST arrays of
+ * `count` device pointers (16-byte aligned, no input overlapping an output); d_ws is a
+ * 256-byte aligned device workspace of at least bf_gc_batch_workspace_size bytes.  The
+ * first call, and any call whose pointers differ from the previous one, captures the
+ * launches into a CUDA graph (on internal streams, thread-local capture mode); every call
+ * then launches that graph on `stream`, so a repeated call costs one graph launch on the
+ * host.  Per-image diagnostics are not kept (each branch reuses one diagnostics header);
+ * use bf_gc_forward and bf_gc_diagnostics on a plan to inspect one image. */
+bf_status bf_gc_batch_forward(bf_gc_batch_t batch, const float *const *d_f, float *const *d_out,
+                              void *d_ws, size_t ws_bytes, bf_stream_t stream);
+
+void bf_gc_batch_destroy(bf_gc_batch_t batch);
 
 /* Kernel timing (a tracing aid, off by default).  While enabled, each forward and
  * backward of the plan records a CUDA event before every kernel it launches and one

@@ -15,7 +15,8 @@ LIB_PATH = os.path.join(_HERE, "libbfgc.so")
 
 BF_OK, BF_ERR_INVALID_ARG, BF_ERR_UNSUPPORTED, BF_ERR_NOMEM, BF_ERR_CUDA, BF_ERR_TIMEOUT, \
     BF_ERR_RANGE, BF_ERR_WORKSPACE = range(8)
-BF_OPT_FORM, BF_OPT_PRECISION, BF_OPT_RANGE_L, BF_OPT_RANGE_U, BF_OPT_POLY, BF_OPT_SAVE_CHANNELS = range(1, 7)
+BF_OPT_FORM, BF_OPT_PRECISION, BF_OPT_RANGE_L, BF_OPT_RANGE_U, BF_OPT_POLY, BF_OPT_SAVE_CHANNELS, \
+    BF_OPT_TILE_W = range(1, 8)
 BF_FORM_PLAIN, BF_FORM_FUSED_TC, BF_FORM_RECURSIVE = range(3)
 BF_PREC_FP32, BF_PREC_BF16, BF_PREC_FP16 = range(3)
 BF_POLY_CHEBYSHEV, BF_POLY_TAYLOR = range(2)
@@ -60,6 +61,11 @@ SIGNATURES = {
     "bf_gc_plan_destroy": (None, [_P]),
     "bf_gc_profile_enable": (_I, [_P, _I]),
     "bf_gc_profile_read": (_I, [_P, ctypes.POINTER(bf_kernel_time), _I, ctypes.POINTER(_I)]),
+    "bf_gc_batch_create": (_I, [_I, ctypes.POINTER(_P), _I, ctypes.POINTER(_P)]),
+    "bf_gc_batch_workspace_size": (_I, [_P, ctypes.POINTER(_SZ)]),
+    "bf_gc_batch_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "bf_gc_batch_forward": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P, _SZ, _P]),
+    "bf_gc_batch_destroy": (None, [_P]),
     "bf_direct": (_I, [_I, _I, _D, _D, _P, _P, _P]),
     "bf_status_string": (ctypes.c_char_p, [_I]),
     "bf_version": (ctypes.c_char_p, []),
@@ -196,6 +202,44 @@ def bf_gc_profile_read(plan):
     n = ctypes.c_int(0)
     _check(lib().bf_gc_profile_read(plan, buf, 32, ctypes.byref(n)), "bf_gc_profile_read")
     return {buf[i].name.decode(): (buf[i].total_ms, buf[i].launches) for i in range(min(n.value, 32))}
+
+
+def bf_gc_batch_create(plans, branches):
+    arr = (_P * len(plans))(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in plans])
+    h = ctypes.c_void_p()
+    _check(lib().bf_gc_batch_create(len(plans), arr, int(branches), ctypes.byref(h)), "bf_gc_batch_create")
+    return h
+
+
+def bf_gc_batch_workspace_size(batch):
+    n = ctypes.c_size_t()
+    _check(lib().bf_gc_batch_workspace_size(batch, ctypes.byref(n)), "bf_gc_batch_workspace_size")
+    return n.value
+
+
+def bf_gc_batch_info(batch, count):
+    """(branch of each image, graphs captured so far)."""
+    br = (_I * count)()
+    cap = _I(0)
+    _check(lib().bf_gc_batch_info(batch, br, ctypes.byref(cap)), "bf_gc_batch_info")
+    return list(br), cap.value
+
+
+def bf_gc_batch_forward(batch, fs, outs, ws, stream=None):
+    if len(fs) != len(outs):
+        raise ValueError("fs and outs differ in length")
+    for f, o in zip(fs, outs):
+        _dev_f32(f, "f")
+        _dev_f32(o, "out")
+    pf = (_P * len(fs))(*[t.data_ptr() for t in fs])
+    po = (_P * len(outs))(*[t.data_ptr() for t in outs])
+    _check(lib().bf_gc_batch_forward(batch, pf, po, _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
+           "bf_gc_batch_forward")
+    return outs
+
+
+def bf_gc_batch_destroy(batch):
+    lib().bf_gc_batch_destroy(batch)
 
 
 def bf_direct(f, sigma_s, sigma_r, out=None, stream=None):

@@ -61,7 +61,7 @@ struct Profiler {
 struct bf_gc_plan_s {
     int H, W, N, R, C;
     double sigma_s, sigma_r, L, U;
-    int form, precision, poly, save_channels;
+    int form, precision, poly, save_channels, tile_w;
     bool used;
     // derived (refit on option change)
     double t_c, s_r, mu, kappa, fit_err;

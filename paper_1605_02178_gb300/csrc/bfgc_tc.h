@@ -16,13 +16,14 @@ struct TcGeom {
     int kb_box_rows;  // rows per TMA box (tile rows or half of them)
     // tcgen05 row pass (k_umma.cu)
     int u_rows;       // padded rows per tile: floor(128 / C) (fewer if the octets do not fit)
-    int u_tw;         // output columns per tile (256, or 64 when a > 4)
+    int u_tw;         // output columns per tile: 64, 128 or 256 (default 256, or 64 when a > 4)
     int u_hb;         // 64-column halo blocks on each side: ceil(a / 4)
     int u_nkb;        // 64-column K-blocks of the channel operand: u_tw / 64 + 2 u_hb
     int u_kbb;        // 64-column K-blocks of the Toeplitz operand: ceil((64 + 32a) / 64)
 };
 
-TcGeom tc_geometry(int H, int W, int R, int C);
+// tw: row-pass tile width (64, 128 or 256; 128 and 256 only for a <= 4), 0 for the default
+TcGeom tc_geometry(int H, int W, int R, int C, int tw = 0);
 size_t tc_workspace_bytes(const TcGeom& g, int C);
 bool tc_supported(int R, int C);
 size_t umma_smem_bytes(const TcGeom& g);

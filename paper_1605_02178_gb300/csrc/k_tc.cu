@@ -484,7 +484,7 @@ cudaError_t launch_vpass_a(const float* f, void* Y, float* out, const GcParams& 
 
 }  // namespace
 
-TcGeom tc_geometry(int H, int W, int R, int C) {
+TcGeom tc_geometry(int H, int W, int R, int C, int tw) {
     TcGeom g{};
     g.a = (R + 15) / 16;
     if (g.a < 1) g.a = 1;
@@ -499,7 +499,7 @@ TcGeom tc_geometry(int H, int W, int R, int C) {
     while (g.kb_stages > 2 && (size_t)kFBytes + (size_t)g.kb_stages * vu_stage_bytes(g.a) > 205 * 1024)
         g.kb_stages -= 2;
     // tcgen05 row pass
-    g.u_tw = g.a <= 4 ? 256 : 64;
+    g.u_tw = g.a <= 4 ? (tw == 64 || tw == 128 ? tw : 256) : 64;
     g.u_rows = std::max(1, std::min(128 / std::max(1, C), umma_max_octets() / ((g.u_tw + 32 * g.a) / 8)));
     g.u_hb = (g.a + 3) / 4;
     g.u_nkb = g.u_tw / 64 + 2 * g.u_hb;

@@ -2,7 +2,7 @@
 //
 // GEMM view.  Rows of the product are (padded image row r, channel c) pairs, m = r C + c,
 // up to 128 of them per tile (TR = floor(128 / C) padded rows); columns are output columns
-// (N = 64 per MMA, TW = 256 or 64 per tile); the contraction runs over input columns.
+// (N = 64 per MMA, TW = 64, 128 or 256 per tile); the contraction runs over input columns.
 //   A (128 x K, K-major, 128-byte swizzle, in shared memory): the channels e u^c of the
 //     tile's rows over the input columns x0 - 64 HB .. (generated by the CTA from f);
 //   B (64 x (64 + 32a), K-major, 128-byte swizzle, shared memory): the banded Toeplitz
@@ -118,7 +118,7 @@ __device__ __forceinline__ void fence_before_sync_after() {
 
 // Shared layout (1024-byte aligned): A buffer 0 | A buffer 1 | B | 2 mbarriers | TMEM slot |
 // product-row table.
-template <typename T, int A_>
+template <typename T, int A_, int TW_>
 __global__ void __launch_bounds__(kUmmaThreads, 1) k_build_hpass_umma(const float* __restrict__ f,
                                                                       T* __restrict__ Y, const GcParams p,
                                                                       const Taps t, TcGeom g, DiagHeader* diag) {
@@ -128,7 +128,8 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_build_hpass_umma(const floa
     // a, the tile width and the halo blocks are compile-time so that the MMA issue sequence
     // of one thread unrolls into constant descriptor offsets (a single thread issuing
     // tcgen05.mma has no other warps to hide its own address arithmetic behind)
-    constexpr int a = A_, TW = A_ <= 4 ? 256 : 64, HB = (A_ + 3) / 4;
+    constexpr int a = A_, TW = TW_, HB = (A_ + 3) / 4;
+    static_assert(TW == 64 || TW == 128 || TW == 256, "tile width");
     const int C = p.C, TR = g.u_rows;
     const int M = TR * C;
     const uint32_t a_bytes = (uint32_t)g.u_nkb * 128u * 128u;
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_build_hpass_umma(const floa
     const int q = warp & 3;
     const int ncw = TW >= 128 ? 4 : TW / 32;
     const int cw = warp >> 2;
-    const int cpw = TW / ncw;                          // 64 (TW = 256) or 32 (TW = 64)
+    const int cpw = TW / ncw;                          // 64 (TW = 256) or 32 (TW = 128, 64)
     const int spitch = cpw * 2 + 16;                   // staging row pitch (bytes)
     const int lpr = cpw / 8;                           // 16-byte chunks per staged row: 8 or 4
 
@@ -340,28 +341,40 @@ size_t umma_smem_bytes(const TcGeom& g) {
     return (size_t)2 * g.u_nkb * 128 * 128 + (size_t)g.u_kbb * 64 * 128 + 64 + 128 * 4 + 1024;
 }
 
-template <typename T, int A_>
+template <typename T, int A_, int TW_>
 cudaError_t launch_umma_impl(const float* f, void* Y, const GcParams& p, const Taps& t, const TcGeom& g,
                              DiagHeader* diag, cudaStream_t s, int grid, size_t smem) {
-    auto kern = k_build_hpass_umma<T, A_>;
+    auto kern = k_build_hpass_umma<T, A_, TW_>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, kUmmaThreads, smem, s>>>(f, static_cast<T*>(Y), p, t, g, diag);
     return cudaGetLastError();
 }
 
+// a <= 4: tile widths 64, 128 and 256; a > 4 (two 64-column halo blocks a side): 64 only
+template <typename T, int A_>
+cudaError_t launch_umma_tw(const float* f, void* Y, const GcParams& p, const Taps& t, const TcGeom& g,
+                           DiagHeader* diag, cudaStream_t s, int grid, size_t smem) {
+    if constexpr (A_ <= 4) {
+        if (g.u_tw == 256) return launch_umma_impl<T, A_, 256>(f, Y, p, t, g, diag, s, grid, smem);
+        if (g.u_tw == 128) return launch_umma_impl<T, A_, 128>(f, Y, p, t, g, diag, s, grid, smem);
+    }
+    if (g.u_tw == 64) return launch_umma_impl<T, A_, 64>(f, Y, p, t, g, diag, s, grid, smem);
+    return cudaErrorInvalidValue;
+}
+
 template <typename T>
 cudaError_t launch_umma_a(const float* f, void* Y, const GcParams& p, const Taps& t, const TcGeom& g,
                           DiagHeader* diag, cudaStream_t s, int grid, size_t smem) {
     switch (g.a) {
-    case 1: return launch_umma_impl<T, 1>(f, Y, p, t, g, diag, s, grid, smem);
-    case 2: return launch_umma_impl<T, 2>(f, Y, p, t, g, diag, s, grid, smem);
-    case 3: return launch_umma_impl<T, 3>(f, Y, p, t, g, diag, s, grid, smem);
-    case 4: return launch_umma_impl<T, 4>(f, Y, p, t, g, diag, s, grid, smem);
-    case 5: return launch_umma_impl<T, 5>(f, Y, p, t, g, diag, s, grid, smem);
-    case 6: return launch_umma_impl<T, 6>(f, Y, p, t, g, diag, s, grid, smem);
-    case 7: return launch_umma_impl<T, 7>(f, Y, p, t, g, diag, s, grid, smem);
-    case 8: return launch_umma_impl<T, 8>(f, Y, p, t, g, diag, s, grid, smem);
+    case 1: return launch_umma_tw<T, 1>(f, Y, p, t, g, diag, s, grid, smem);
+    case 2: return launch_umma_tw<T, 2>(f, Y, p, t, g, diag, s, grid, smem);
+    case 3: return launch_umma_tw<T, 3>(f, Y, p, t, g, diag, s, grid, smem);
+    case 4: return launch_umma_tw<T, 4>(f, Y, p, t, g, diag, s, grid, smem);
+    case 5: return launch_umma_tw<T, 5>(f, Y, p, t, g, diag, s, grid, smem);
+    case 6: return launch_umma_tw<T, 6>(f, Y, p, t, g, diag, s, grid, smem);
+    case 7: return launch_umma_tw<T, 7>(f, Y, p, t, g, diag, s, grid, smem);
+    case 8: return launch_umma_tw<T, 8>(f, Y, p, t, g, diag, s, grid, smem);
     default: return cudaErrorInvalidValue;
     }
 }

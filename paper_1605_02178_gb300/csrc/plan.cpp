@@ -136,7 +136,7 @@ size_t fwd_workspace(const bf_gc_plan_s* p) {
     case BF_FORM_PLAIN:
         return BF_WS_HEADER + 2 * (size_t)p->C * bfgc::plain_plane_stride(p->H, p->W) * sizeof(float);
     case BF_FORM_FUSED_TC:
-        return BF_WS_HEADER + round_up(bfgc::tc_workspace_bytes(bfgc::tc_geometry(p->H, p->W, p->R, p->C), p->C), 256);
+        return BF_WS_HEADER + round_up(bfgc::tc_workspace_bytes(bfgc::tc_geometry(p->H, p->W, p->R, p->C, p->tile_w), p->C), 256);
     case BF_FORM_RECURSIVE:
         return BF_WS_HEADER + 2 * (size_t)p->C * bfgc::plain_plane_stride(p->H, p->W) * sizeof(float) +
                (size_t)p->C * std::max(p->H, p->W) * p->R * sizeof(float);
@@ -237,7 +237,7 @@ bf_status bf_gc_plan(int H, int W, double sigma_s, double sigma_r, int N, bf_gc_
     p->sigma_s = sigma_s; p->sigma_r = sigma_r;
     p->L = 0.0; p->U = 255.0;
     p->form = BF_FORM_PLAIN; p->precision = BF_PREC_FP32; p->poly = BF_POLY_CHEBYSHEV;
-    p->save_channels = 0; p->used = false;
+    p->save_channels = 0; p->tile_w = 0; p->used = false;
     refit(p);
     make_taps(sigma_s, R, &p->taps);
     *out = p;
@@ -274,6 +274,11 @@ bf_status bf_gc_plan_set(bf_gc_plan_t p, int option, double value) {
     case BF_OPT_SAVE_CHANNELS:
         if (iv != value || (iv != 0 && iv != 1)) return BF_ERR_INVALID_ARG;
         p->save_channels = iv;
+        return BF_OK;
+    case BF_OPT_TILE_W:
+        if (iv != value || (iv != 0 && iv != 64 && iv != 128 && iv != 256)) return BF_ERR_INVALID_ARG;
+        if (iv > 64 && (p->R + 15) / 16 > 4) return BF_ERR_UNSUPPORTED;
+        p->tile_w = iv;
         return BF_OK;
     default:
         return BF_ERR_INVALID_ARG;
@@ -332,7 +337,7 @@ bf_status bf_gc_forward(bf_gc_plan_t p, const float* f, float* out, void* ws, si
         break;
     }
     case BF_FORM_FUSED_TC: {
-        const bfgc::TcGeom g = bfgc::tc_geometry(p->H, p->W, p->R, p->C);
+        const bfgc::TcGeom g = bfgc::tc_geometry(p->H, p->W, p->R, p->C, p->tile_w);
         const bool fp16 = p->precision == BF_PREC_FP16;
         prof_mark(p, "build_hpass_tc", s);
         if ((e = bfgc::launch_build_hpass_umma(f, body, p->gp, p->taps, g, fp16, diag, s)) != cudaSuccess) break;
