@@ -58,10 +58,12 @@ enum {
     BF_OPT_POLY = 5,          /* value: BF_POLY_*, choice of c_n                   (default CHEB)  */
     BF_OPT_SAVE_CHANNELS = 6, /* value: 1 = forward leaves the filtered channels in the workspace
                                  for bf_gc_backward to reuse; 0 = backward recomputes them      */
-    BF_OPT_TILE_W = 7         /* value: output columns per tile of the tensor-core row pass: 0
-                                 (default: 256 when ceil(R/16) <= 4, else 64), 64, 128 or 256;
-                                 128 and 256 need ceil(R/16) <= 4 (else BF_ERR_UNSUPPORTED).
-                                 The result does not depend on it (same products, same order). */
+    BF_OPT_TILE_W = 7         /* value: row-pass kernel of the tensor-core form.  0 (default):
+                                 Toeplitz operand in tensor memory, tiles of 128 output columns.
+                                 64, 128 or 256: Toeplitz operand in shared memory, tiles of that
+                                 many output columns (128 and 256 need ceil(R/16) <= 4, else
+                                 BF_ERR_UNSUPPORTED).  The three widths give identical results;
+                                 the default kernel sums the same products in another order. */
 };
 enum {
     BF_FORM_PLAIN = 0,        /* 4 kernels: build F_n -> row filter -> column filter -> ratio; FP32 */

@@ -1,11 +1,14 @@
 """Autotuner for batched filtering, with a JSON cache.
 
-Two choices are tuned, neither of which changes any result:
-  * the tile width (64, 128 or 256 output columns) of the tensor-core row pass, per bucket
-    (a = ceil(R / 16), C = N + 2, width class, storage precision): the candidates are timed
-    on a small batch of synthetic images of that bucket, run as one graph, so the choice is
-    the one with the best throughput when images share the GPU;
-  * the number of concurrent graph branches of a batch, per batch composition.
+Two choices are tuned:
+  * the row-pass kernel of the tensor-core form (BF_OPT_TILE_W: 0 = Toeplitz operand in
+    tensor memory, 64 / 128 / 256 = Toeplitz operand in shared memory with tiles of that
+    width), per bucket (a = ceil(R / 16), C = N + 2, width class, storage precision): the
+    candidates are timed on a small batch of synthetic images of that bucket, run as one
+    graph, so the choice is the one with the best throughput when images share the GPU.  The
+    three widths give identical results; kernel 0 sums the same products in another order;
+  * the number of concurrent graph branches of a batch, per batch composition (no effect on
+    any result).
 The cache maps "<device name>" -> {"tile_w": {bucket: width}, "branches": {signature: k}}
 and is written after every new measurement.  `measure` can be replaced (tests use a fake
 timer) and is called as measure(kind, **params) -> milliseconds.
@@ -14,7 +17,7 @@ import json
 import os
 import threading
 
-TILE_WIDTHS = (64, 128, 256)
+TILE_WIDTHS = (0, 64, 128, 256)
 BRANCH_COUNTS = (1, 2, 4, 8, 16)
 WIDTH_CLASSES = ((192, 128), (640, 512), (None, 1536))   # (upper bound of W, representative W)
 
@@ -82,17 +85,16 @@ class Autotuner:
 
     # ---- choices
     def tile_w(self, R, C, W, precision="bf16"):
-        """Row-pass tile width for images of this bucket (64 whenever a > 4)."""
+        """BF_OPT_TILE_W for images of this bucket (widths 128 and 256 only when a <= 4)."""
         a = max(1, (int(R) + 15) // 16)
-        if a > 4:
-            return 64
+        cands = TILE_WIDTHS if a <= 4 else (0, 64)
         key = tile_bucket(R, C, W, precision)
         with self._lock:
             e = self._entry()
             if key not in e["tile_w"]:
                 times = {tw: self.measure("tile_w", a=a, C=int(C), W=WIDTH_CLASSES[width_class(W)][1],
-                                          precision=precision, tile_w=tw) for tw in TILE_WIDTHS}
-                e["tile_w"][key] = min(TILE_WIDTHS, key=lambda tw: (times[tw], -tw))
+                                          precision=precision, tile_w=tw) for tw in cands}
+                e["tile_w"][key] = min(cands, key=lambda tw: (times[tw], tw))
                 self.save()
             return int(e["tile_w"][key])
 

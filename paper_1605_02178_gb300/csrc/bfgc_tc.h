@@ -1,5 +1,6 @@
-// Geometry and launchers of the fused tensor-core form (k_umma.cu: row pass, k_tc.cu:
-// column pass + ratio).
+// Geometry and launchers of the fused tensor-core form (k_rows_tc.cu: row pass with the
+// Toeplitz operand in tensor memory, the default; k_umma.cu: row pass with the Toeplitz
+// operand in shared memory and a chosen tile width; k_tc.cu: column pass + ratio).
 #pragma once
 
 #include "bfgc_internal.h"
@@ -8,18 +9,21 @@ namespace bfgc {
 
 // Row-filtered channel buffer Y[p][c][x]: Hp padded rows, each holding the C channel rows of
 // Wp columns, 2-byte elements.  Padded row p holds image row p - P (mirrored into [0, H));
-// P = 16a rows of margin above and below, Hp = round_up(H, 64) + 2P, Wp = round_up(W, 64).
+// P = 16a rows of margin above and below, Hp = round_up(H, 128) + 2P, Wp = round_up(W, 64).
 struct TcGeom {
     int a;            // ceil(R / 16): Toeplitz k-blocks on each side of an output block
     int P, Hp, Wp;
     int kb_stages;    // TMA ring depth of the column pass kernel
     int kb_box_rows;  // rows per TMA box (tile rows or half of them)
-    // tcgen05 row pass (k_umma.cu)
+    // tcgen05 row pass with the Toeplitz operand in shared memory (k_umma.cu)
     int u_rows;       // padded rows per tile: floor(128 / C) (fewer if the octets do not fit)
     int u_tw;         // output columns per tile: 64, 128 or 256 (default 256, or 64 when a > 4)
     int u_hb;         // 64-column halo blocks on each side: ceil(a / 4)
     int u_nkb;        // 64-column K-blocks of the channel operand: u_tw / 64 + 2 u_hb
     int u_kbb;        // 64-column K-blocks of the Toeplitz operand: ceil((64 + 32a) / 64)
+    // tcgen05 row pass with the Toeplitz operand in tensor memory (k_rows_tc.cu)
+    int r_rows;       // padded rows per tile: floor(128 / C) (fewer if the octets do not fit)
+    int r_stages;     // channel-buffer ring depth (2 .. 4)
 };
 
 // tw: row-pass tile width (64, 128 or 256; 128 and 256 only for a <= 4), 0 for the default
@@ -28,6 +32,11 @@ size_t tc_workspace_bytes(const TcGeom& g, int C);
 bool tc_supported(int R, int C);
 size_t umma_smem_bytes(const TcGeom& g);
 int umma_max_octets();
+int rows_tc_max_octets();
+size_t rows_tc_stage_bytes(int a);
+size_t rows_tc_smem_bytes(const TcGeom& g);
+cudaError_t launch_build_hpass_tc(const float* f, void* Y, const GcParams& p, const Taps& t, const TcGeom& g,
+                                  bool fp16, DiagHeader* diag, cudaStream_t s);
 cudaError_t launch_build_hpass_umma(const float* f, void* Y, const GcParams& p, const Taps& t, const TcGeom& g,
                                     bool fp16, DiagHeader* diag, cudaStream_t s);
 cudaError_t launch_vpass_combine_tc(const float* f, void* Y, float* out, const GcParams& p, const Taps& t,

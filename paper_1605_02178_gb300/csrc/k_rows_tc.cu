@@ -1,0 +1,454 @@
+// Channel build + row pass of eq. (7) on the 5th-generation tensor cores (tcgen05), with the
+// Toeplitz operand in tensor memory and the output columns on the accumulator lanes.
+//
+// GEMM view, per tile of 128 output columns (x0 .. x0 + 127) and TR padded rows:
+//   D[x][m] = sum_k A[x][k] B[m][k],   k = 0 .. KIN - 1,  KIN = 128 + 32a,
+//   A[x][k] = g(k - 16a - x), zero where |k - 16a - x| > R: the banded Toeplitz matrix of the
+//     row Gaussian, 128 x KIN, written once into TENSOR memory (lane x, 32-bit column c =
+//     elements 2c, 2c + 1), so that the MMAs read only B from shared memory;
+//   B[m][k] = the channel e u^c of padded row r at input column x0 - 16a + k, m = r C + c
+//     (K-major, 128-byte swizzle, 64-column K-blocks of 128 rows), generated by the CTA from f;
+//   D = 128 lanes (output columns) x 128 fp32 columns (product rows m), one of two
+//     accumulator buffers.
+// 8 + 2a MMAs of 128 x 128 x 16 per tile: 128 + 32a multiply-adds per output and channel.
+// An accumulator lane holds one output column for every (row, channel) pair, so the drain
+// stores each product row of 128 columns straight to Y from registers: neighbouring lanes
+// swap one value (a shuffle) so that every store writes two adjacent BF16/FP16 columns, and
+// a warp's store covers two 64-byte runs of two product rows.
+//
+// Roles (persistent CTA, one per SM, warp-specialised; the phases of a tile meet at mbarriers
+// only):
+//   warps 8 .. 15 : channel build into an S-stage ring of B buffers (full / empty barriers);
+//                   the f values of the next tile are fetched into registers while waiting;
+//   warp 16, one lane : MMA issuer; a tile's MMAs are committed to the stage's empty barrier
+//                   and to the accumulator buffer's full barrier;
+//   warps 0 .. 7  : drain, two per tensor-memory lane quarter, 64 product rows each.
+// Every mbarrier wait is bounded; a wait that runs out flags the workspace and raises a shared
+// abort flag that ends the other roles' waits, so the kernel always returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
+#include "bfgc_common.cuh"
+#include "bfgc_tc.h"
+
+namespace bfgc {
+
+namespace {
+
+constexpr int kRDrainWarps = 8;
+constexpr int kRGenWarps = 8;
+constexpr int kRThreads = 32 * (kRDrainWarps + kRGenWarps + 1);
+constexpr int kRGenThreads = 32 * kRGenWarps;
+constexpr int kROctSlots = 3;                     // 8-column octets per build thread per tile
+constexpr unsigned kRWaitNs = 1000000000u;        // bound of one mbarrier wait (1 s)
+constexpr unsigned kRSuspendNs = 20000u;          // suspend-time hint of one try_wait
+constexpr int kRTile = 128;                       // output columns per tile (accumulator lanes)
+constexpr int kRN = 128;                          // product rows per tile (accumulator columns)
+constexpr int kRStageBytesPerKb = kRN * 128;      // one 64-column K-block of B
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(su32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" :: "r"(su32(bar)) : "memory");
+}
+// try_wait with a suspend-time hint: a waiting warp sleeps until the phase completes (or the
+// hint runs out) instead of spinning and taking issue slots from the working warps
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(su32(bar)), "r"(parity), "r"(kRSuspendNs) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of parity `parity` of `bar` (every waiter walks its barrier's phases in
+// order, so the phase before the awaited one is complete).  Gives up when another role raised
+// the abort flag, or (raising it and flagging the workspace) after kRWaitNs.
+__device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, unsigned parity, volatile int* abort_flag,
+                                                DiagHeader* diag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (global_ns() - t0 > kRWaitNs) break;
+    }
+    *abort_flag = 1;
+    atomicOr(&diag->error_flags, 4u);
+    return false;
+}
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, unsigned parity) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity) && global_ns() - t0 <= kRWaitNs) {
+    }
+}
+
+// Two FP32 lanes in one 64-bit register: packed multiply (one instruction for two products)
+__device__ __forceinline__ uint64_t f2_make(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_split(uint64_t a, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// FP16 channels are stored times 2^14: |e u^n| <= 1, so the scaled channels and their
+// Gaussian averages stay below 2^14 (FP16 max 65504), while the high powers of mid-range
+// pixels move out of the FP16 subnormal range.  A power of two is exact, and a common
+// factor of every channel cancels in P/Q and in the relative division guard.
+template <typename T> struct kChannelScale { static constexpr float value = 1.0f; };
+template <> struct kChannelScale<__half> { static constexpr float value = 16384.0f; };
+
+template <typename T> __device__ __forceinline__ uint32_t pack2(float lo, float hi);
+template <> __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+template <> __device__ __forceinline__ uint32_t pack2<__half>(float lo, float hi) {
+    __half2 v = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
+    // load and wait in one statement: the registers are defined only once the wait is done
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                 "tcgen05.wait::ld.sync.aligned;\n"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+                   "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+                   "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                 : "r"(taddr) : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* r) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n"
+                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+
+}  // namespace
+
+// Shared layout (1024-byte aligned): S stages of KB K-blocks | full[S] | empty[S] | dfull[2] |
+// dempty[2] | TMEM slot | abort flag | last tile committed per accumulator buffer [2].
+template <typename T, int A_>
+__global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const float* __restrict__ f, T* __restrict__ Y,
+                                                                 const GcParams p, const Taps t, TcGeom g,
+                                                                 DiagHeader* diag) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
+    constexpr int a = A_, KIN = kRTile + 32 * A_, KS = KIN / 16, KB = (KIN + 63) / 64, NO = KIN / 8;
+    constexpr int ACOLS = KIN / 2;                     // tensor-memory columns of A
+    constexpr uint32_t SB = (uint32_t)KB * kRStageBytesPerKb;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int C = p.C, TR = g.r_rows, S = g.r_stages, M = TR * C;
+    unsigned char* stages = smem;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * SB);
+    uint64_t* empty = full + S;
+    uint64_t* dfull = empty + S;
+    uint64_t* dempty = dfull + 2;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(dempty + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    volatile int* last_d = abort_flag + 1;
+    const int tiles_x = (g.Wp + kRTile - 1) / kRTile, tiles_y = (g.Hp + TR - 1) / TR;
+    const int ntiles = tiles_x * tiles_y, G = gridDim.x;
+    const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;
+
+    // ---- set-up: TMEM, barriers, row table, zero product rows M .. 127 of every stage
+    if (warp == kRDrainWarps + kRGenWarps) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" :: "r"(su32(tslot)), "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], kRGenThreads);
+            mbar_init(&empty[s], 1);
+        }
+        for (int d = 0; d < 2; ++d) {
+            mbar_init(&dfull[d], 1);
+            mbar_init(&dempty[d], kRDrainWarps);
+            last_d[d] = -1;
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    for (int idx = tid; idx < S * (kRN - M) * KB * 8; idx += blockDim.x) {      // 16-byte chunks
+        const int s = idx / ((kRN - M) * KB * 8), rem = idx % ((kRN - M) * KB * 8);
+        const int row = M + rem / (KB * 8), ch = rem % (KB * 8);
+        const int kb = ch >> 3, c16 = ch & 7;
+        *reinterpret_cast<uint4*>(stages + (size_t)s * SB + (uint32_t)kb * kRStageBytesPerKb + (row >> 3) * 1024 +
+                                  (row & 7) * 128 + ((c16 ^ (row & 7)) << 4)) = make_uint4(0, 0, 0, 0);
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tbase = *tslot;
+    const uint32_t tacc = tbase + 256u;                // accumulator buffers: columns 256 .. 511
+
+    // ---- the Toeplitz operand into tensor memory: warp q < 4 writes lanes 32q .. 32q + 31
+    if (warp < 4) {
+        const int i = 32 * warp + lane;
+        auto tap = [&](int k) {
+            const int d = k - 16 * a - i, ad = d < 0 ? -d : d;
+            return ad <= t.R ? t.g[ad] : 0.0f;
+        };
+        for (int c0 = 0; c0 < ACOLS; c0 += 8) {
+            uint32_t r[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) r[e] = pack2<T>(tap(2 * (c0 + e)), tap(2 * (c0 + e) + 1));
+            tmem_st8(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, r);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+
+    if (warp >= kRDrainWarps && warp < kRDrainWarps + kRGenWarps) {
+        // ------------------------------------------------------------ channel build
+        const int gtid = tid - 32 * kRDrainWarps;
+        const int noct = TR * NO;                      // <= kRGenThreads * kROctSlots (host checks)
+        const bool vec = (p.W & 3) == 0;               // 16-byte aligned rows of f
+        float fv[kROctSlots][8];
+        auto load_f = [&](int tile) {
+            const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+            const int p0 = ty * TR, xs0 = tx * kRTile - 16 * a;
+#pragma unroll
+            for (int s = 0; s < kROctSlots; ++s) {
+                const int o = gtid + s * kRGenThreads;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) fv[s][e] = 0.0f;
+                if (tile < ntiles && o < noct) {
+                    const int r = o / NO, j = o - r * NO;
+                    const int pr = p0 + r;
+                    if (pr < g.Hp) {
+                        int y = pr - g.P;
+                        y = (unsigned)y < (unsigned)p.H ? y : mirror(y, p.H);
+                        const float* frow = f + (size_t)y * p.W;
+                        const int xs = xs0 + 8 * j;
+                        if (vec && xs >= 0 && xs + 8 <= p.W) {
+                            const float4 a0 = __ldg(reinterpret_cast<const float4*>(frow + xs));
+                            const float4 a1 = __ldg(reinterpret_cast<const float4*>(frow + xs + 4));
+                            fv[s][0] = a0.x; fv[s][1] = a0.y; fv[s][2] = a0.z; fv[s][3] = a0.w;
+                            fv[s][4] = a1.x; fv[s][5] = a1.y; fv[s][6] = a1.z; fv[s][7] = a1.w;
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                const int x = xs + e;
+                                fv[s][e] = __ldg(frow + ((unsigned)x < (unsigned)p.W ? x : mirror(x, p.W)));
+                            }
+                        }
+                    }
+                }
+            }
+        };
+        load_f((int)blockIdx.x);
+        for (int it = 0; it < my_tiles; ++it) {
+            const int s = it % S, use = it / S;
+            if (use > 0 && !mbar_wait_abort(&empty[s], (unsigned)((use - 1) & 1), abort_flag, diag)) break;
+            unsigned char* B = stages + (size_t)s * SB;
+            // channels e u^c of the fetched octets: 8 independent power chains per octet, one
+            // 16-byte shared store per channel
+#pragma unroll
+            for (int sl = 0; sl < kROctSlots; ++sl) {
+                const int o = gtid + sl * kRGenThreads;
+                if (o >= noct) continue;
+                const int r = o / NO, j = o - r * NO;
+                const int k0 = 8 * j;
+                const int chunk = (k0 & 63) >> 3;
+                float u[8], e0[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    u[e] = (fv[sl][e] - p.t_c) * p.inv_sr;
+                    e0[e] = expf(-p.half_mu * u[e] * u[e]) * kChannelScale<T>::value;
+                }
+                uint64_t u2[4], v2[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    u2[e] = f2_make(u[2 * e], u[2 * e + 1]);
+                    v2[e] = f2_make(e0[2 * e], e0[2 * e + 1]);
+                }
+                int mrow = r * C;
+                unsigned char* Bk = B + (uint32_t)(k0 >> 6) * kRStageBytesPerKb;
+                for (int c = 0; c < C; ++c, ++mrow) {
+                    uint4 w;
+                    float lo, hi;
+                    f2_split(v2[0], lo, hi); w.x = pack2<T>(lo, hi);
+                    f2_split(v2[1], lo, hi); w.y = pack2<T>(lo, hi);
+                    f2_split(v2[2], lo, hi); w.z = pack2<T>(lo, hi);
+                    f2_split(v2[3], lo, hi); w.w = pack2<T>(lo, hi);
+                    *reinterpret_cast<uint4*>(Bk + (uint32_t)mrow * 128u + (uint32_t)((chunk ^ (mrow & 7)) << 4)) = w;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) v2[e] = f2_mul(v2[e], u2[e]);
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            mbar_arrive(&full[s]);
+            load_f((int)blockIdx.x + (it + 1) * G);
+        }
+    } else if (warp == kRDrainWarps + kRGenWarps) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            // D f32 (bit 4); A, B f16 (0) or bf16 (1) at bits 7, 10; both K-major (bits 15, 16
+            // zero); N / 8 at bit 17, M / 16 at bit 24
+            const uint32_t fmt = std::is_same<T, __half>::value ? 0u : 1u;
+            const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kRN >> 3) << 17) |
+                                   ((uint32_t)(kRTile >> 4) << 24);
+            for (int it = 0; it < my_tiles; ++it) {
+                const int s = it % S, use = it / S, d = it & 1, duse = it >> 1;
+                if (!mbar_wait_abort(&full[s], (unsigned)(use & 1), abort_flag, diag)) break;
+                if (duse > 0 && !mbar_wait_abort(&dempty[d], (unsigned)((duse - 1) & 1), abort_flag, diag)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint64_t b0 = sw128_desc(su32(stages + (size_t)s * SB));
+                const uint32_t dt = tacc + (uint32_t)(d * kRN);
+#pragma unroll
+                for (int ks = 0; ks < KS; ++ks) {
+                    // A: 8 tensor-memory columns per k-step; B: 32 bytes per k-step inside a
+                    // 64-column K-block, K-blocks kRStageBytesPerKb apart
+                    const uint64_t bd =
+                        b0 + (uint64_t)(((uint32_t)(ks >> 2) * kRStageBytesPerKb + (uint32_t)(ks & 3) * 32u) >> 4);
+                    asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+                                 " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, q;\n}\n"
+                                 :: "r"(dt), "r"(tbase + (uint32_t)(8 * ks)), "l"(bd), "r"(idesc),
+                                    "r"(ks > 0 ? 1u : 0u));
+                }
+                last_d[d] = it;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                             :: "r"(su32(&empty[s])) : "memory");
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                             :: "r"(su32(&dfull[d])) : "memory");
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ drain
+        const int q = warp & 3, h = warp >> 2;         // lane quarter, half of the product rows
+        const bool odd = lane & 1;
+        for (int it = 0; it < my_tiles; ++it) {
+            const int d = it & 1, duse = it >> 1;
+            bool w = true;
+            if (lane == 0) w = mbar_wait_abort(&dfull[d], (unsigned)(duse & 1), abort_flag, diag);
+            if (!__shfl_sync(0xffffffffu, w, 0)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            uint32_t v0[32], v1[32];
+            const uint32_t tl = tacc + ((uint32_t)(32 * q) << 16) + (uint32_t)(d * kRN + 64 * h);
+            tmem_ld32(tl, v0);
+            tmem_ld32(tl + 32u, v1);
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&dempty[d]);
+            const int tile = (int)blockIdx.x + it * G;
+            const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+            const int p0 = ty * TR;
+            // product row m = r C + c of the tile is row p0 C + m of Y (viewed as Hp C rows of
+            // Wp columns); rows from mlim on are padding or past the last padded row
+            const int mlim = min(M, (g.Hp - p0) * C);
+            // this lane's output column; each pair of lanes stores columns xe, xe + 1
+            const int xe = tx * kRTile + 32 * q + (lane & ~1);
+            const bool xok = xe < g.Wp;
+            T* Yb = Y + (size_t)p0 * C * g.Wp + xe;
+            auto store_pairs = [&](const uint32_t* v, int m0) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    // even lane: product row m0 + 2j, odd lane: m0 + 2j + 1
+                    const float mine = __uint_as_float(odd ? v[2 * j + 1] : v[2 * j]);
+                    const float give = __uint_as_float(odd ? v[2 * j] : v[2 * j + 1]);
+                    const float other = __shfl_xor_sync(0xffffffffu, give, 1);
+                    const int m = m0 + 2 * j + (odd ? 1 : 0);
+                    if (m < mlim && xok) {
+                        const uint32_t w2 = odd ? pack2<T>(other, mine) : pack2<T>(mine, other);
+                        *reinterpret_cast<uint32_t*>(Yb + (size_t)m * g.Wp) = w2;
+                    }
+                }
+            };
+            store_pairs(v0, 64 * h);
+            store_pairs(v1, 64 * h + 32);
+        }
+    }
+
+    // ---- drain: every MMA committed has completed (immediate unless a wait gave up), then
+    // release tensor memory
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+        for (int d = 0; d < 2; ++d)
+            if (last_d[d] >= 0) mbar_drain(&dfull[d], (unsigned)((last_d[d] >> 1) & 1));
+    }
+    __syncthreads();
+    if (warp == kRDrainWarps + kRGenWarps) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tbase), "r"(512));
+    }
+}
+
+int rows_tc_max_octets() { return kRGenThreads * kROctSlots; }
+
+size_t rows_tc_stage_bytes(int a) { return (size_t)((kRTile + 32 * a + 63) / 64) * kRStageBytesPerKb; }
+
+size_t rows_tc_smem_bytes(const TcGeom& g) {
+    return (size_t)g.r_stages * rows_tc_stage_bytes(g.a) + (2 * g.r_stages + 4) * 8 + 16 + 1024;
+}
+
+template <typename T, int A_>
+cudaError_t launch_rows_impl(const float* f, void* Y, const GcParams& p, const Taps& t, const TcGeom& g,
+                             DiagHeader* diag, cudaStream_t s) {
+    const size_t smem = rows_tc_smem_bytes(g);
+    auto kern = k_build_hpass_tc<T, A_>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int tiles = ((g.Wp + kRTile - 1) / kRTile) * ((g.Hp + g.r_rows - 1) / g.r_rows);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::max(1, std::min(tiles, sms));
+    kern<<<grid, kRThreads, smem, s>>>(f, static_cast<T*>(Y), p, t, g, diag);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_rows_a(const float* f, void* Y, const GcParams& p, const Taps& t, const TcGeom& g,
+                          DiagHeader* diag, cudaStream_t s) {
+    switch (g.a) {
+    case 1: return launch_rows_impl<T, 1>(f, Y, p, t, g, diag, s);
+    case 2: return launch_rows_impl<T, 2>(f, Y, p, t, g, diag, s);
+    case 3: return launch_rows_impl<T, 3>(f, Y, p, t, g, diag, s);
+    case 4: return launch_rows_impl<T, 4>(f, Y, p, t, g, diag, s);
+    case 5: return launch_rows_impl<T, 5>(f, Y, p, t, g, diag, s);
+    case 6: return launch_rows_impl<T, 6>(f, Y, p, t, g, diag, s);
+    case 7: return launch_rows_impl<T, 7>(f, Y, p, t, g, diag, s);
+    case 8: return launch_rows_impl<T, 8>(f, Y, p, t, g, diag, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_build_hpass_tc(const float* f, void* Y, const GcParams& p, const Taps& t, const TcGeom& g,
+                                  bool fp16, DiagHeader* diag, cudaStream_t s) {
+    return fp16 ? launch_rows_a<__half>(f, Y, p, t, g, diag, s) : launch_rows_a<__nv_bfloat16>(f, Y, p, t, g, diag, s);
+}
+
+}  // namespace bfgc

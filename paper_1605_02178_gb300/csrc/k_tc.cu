@@ -498,12 +498,14 @@ TcGeom tc_geometry(int H, int W, int R, int C, int tw) {
     g.kb_stages = 8;
     while (g.kb_stages > 2 && (size_t)kFBytes + (size_t)g.kb_stages * vu_stage_bytes(g.a) > 205 * 1024)
         g.kb_stages -= 2;
-    // tcgen05 row pass
+    // tcgen05 row passes (shared-memory Toeplitz; tensor-memory Toeplitz)
     g.u_tw = g.a <= 4 ? (tw == 64 || tw == 128 ? tw : 256) : 64;
     g.u_rows = std::max(1, std::min(128 / std::max(1, C), umma_max_octets() / ((g.u_tw + 32 * g.a) / 8)));
     g.u_hb = (g.a + 3) / 4;
     g.u_nkb = g.u_tw / 64 + 2 * g.u_hb;
     g.u_kbb = (64 + 32 * g.a + 63) / 64;
+    g.r_rows = std::max(1, std::min(128 / std::max(1, C), rows_tc_max_octets() / ((128 + 32 * g.a) / 8)));
+    g.r_stages = (int)std::min<size_t>(4, (size_t)(200 * 1024) / rows_tc_stage_bytes(g.a));
     return g;
 }
 
@@ -512,7 +514,8 @@ size_t tc_workspace_bytes(const TcGeom& g, int C) { return (size_t)C * g.Hp * g.
 bool tc_supported(int R, int C) {
     if (R > 16 * BF_TC_MAX_A || C > 128) return false;
     const TcGeom g = tc_geometry(64, 64, R, C);
-    return umma_smem_bytes(g) <= 227 * 1024 && vu_smem_bytes(g) <= 227 * 1024 && vu_bufs(g.a) >= 2;
+    return umma_smem_bytes(g) <= 227 * 1024 && vu_smem_bytes(g) <= 227 * 1024 && vu_bufs(g.a) >= 2 &&
+           g.r_stages >= 2 && rows_tc_smem_bytes(g) <= 227 * 1024;
 }
 
 cudaError_t launch_vpass_combine_tc(const float* f, void* Y, float* out, const GcParams& p, const Taps& t,

@@ -1,4 +1,6 @@
-// Channel build + row pass of eq. (7) on the 5th-generation tensor cores (tcgen05).
+// Channel build + row pass of eq. (7) on the 5th-generation tensor cores (tcgen05), with the
+// Toeplitz operand in shared memory: the variant selected by BF_OPT_TILE_W = 64, 128 or 256
+// (the default row pass, k_rows_tc.cu, holds the Toeplitz operand in tensor memory).
 //
 // GEMM view.  Rows of the product are (padded image row r, channel c) pairs, m = r C + c,
 // up to 128 of them per tile (TR = floor(128 / C) padded rows); columns are output columns

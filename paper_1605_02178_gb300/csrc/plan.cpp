@@ -340,7 +340,10 @@ bf_status bf_gc_forward(bf_gc_plan_t p, const float* f, float* out, void* ws, si
         const bfgc::TcGeom g = bfgc::tc_geometry(p->H, p->W, p->R, p->C, p->tile_w);
         const bool fp16 = p->precision == BF_PREC_FP16;
         prof_mark(p, "build_hpass_tc", s);
-        if ((e = bfgc::launch_build_hpass_umma(f, body, p->gp, p->taps, g, fp16, diag, s)) != cudaSuccess) break;
+        // row pass: the Toeplitz operand in tensor memory (default), or in shared memory with
+        // the tile width the plan asks for
+        if ((e = p->tile_w ? bfgc::launch_build_hpass_umma(f, body, p->gp, p->taps, g, fp16, diag, s)
+                           : bfgc::launch_build_hpass_tc(f, body, p->gp, p->taps, g, fp16, diag, s)) != cudaSuccess) break;
         prof_mark(p, "vpass_combine_tc", s);
         e = bfgc::launch_vpass_combine_tc(f, body, out, p->gp, p->taps, g, fp16, diag, s);
         break;

@@ -116,17 +116,17 @@ def test_autotuner_picks_fastest_and_caches(tmp_path):
 
     def fake(kind, **kw):
         calls.append((kind, kw["tile_w"]))
-        return {64: 3.0, 128: 1.0, 256: 2.0}[kw["tile_w"]]
+        return {0: 1.5, 64: 3.0, 128: 1.0, 256: 2.0}[kw["tile_w"]]
 
     t = autotune.Autotuner(path=str(path), device_name="fake-gpu", measure=fake)
     assert t.tile_w(30, 10, 1000, "bf16") == 128
-    assert len(calls) == 3
+    assert len(calls) == 4
     assert t.tile_w(30, 10, 900, "bf16") == 128          # same bucket: cached, no new timing
-    assert len(calls) == 3
-    assert t.tile_w(90, 10, 900, "bf16") == 64           # a = 6: only 64 exists, nothing timed
-    assert len(calls) == 3
+    assert len(calls) == 4
+    assert t.tile_w(90, 10, 900, "bf16") == 0            # a = 6: only kernels 0 and 64 exist
+    assert len(calls) == 6 and {c[1] for c in calls[4:]} == {0, 64}
     t.tile_w(30, 10, 100, "bf16")                        # another width class
-    assert len(calls) == 6
+    assert len(calls) == 10
     assert t.branches("sig", lambda k: {1: 9, 2: 5, 4: 3, 8: 3, 16: 4}[k]) == 4   # ties: fewer branches
     data = json.loads(path.read_text())
     assert data["fake-gpu"]["tile_w"][autotune.tile_bucket(30, 10, 1000, "bf16")] == 128
@@ -137,7 +137,7 @@ def test_autotuner_picks_fastest_and_caches(tmp_path):
     assert t2.tile_w(30, 10, 1000, "bf16") == 128
     assert t2.branches("sig", lambda k: pytest.fail("timed a cached batch")) == 4
     # another device name has its own entries
-    t3 = autotune.Autotuner(path=str(path), device_name="other", measure=lambda kind, **kw: 1.0 / kw["tile_w"])
+    t3 = autotune.Autotuner(path=str(path), device_name="other", measure=lambda kind, **kw: 1.0 / (1 + kw["tile_w"]))
     assert t3.tile_w(30, 10, 1000, "bf16") == 256
     assert json.loads(path.read_text())["fake-gpu"]["tile_w"][autotune.tile_bucket(30, 10, 1000, "bf16")] == 128
 
@@ -146,7 +146,7 @@ def test_autotuner_survives_a_corrupt_cache(tmp_path):
     path = tmp_path / "tune.json"
     path.write_text("{not json")
     t = autotune.Autotuner(path=str(path), device_name="g", measure=lambda kind, **kw: kw["tile_w"])
-    assert t.tile_w(10, 6, 64, "fp16") == 64
+    assert t.tile_w(10, 6, 64, "fp16") == 0
     assert json.loads(path.read_text())["g"]["tile_w"]
 
 

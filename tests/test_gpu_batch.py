@@ -25,11 +25,11 @@ def _images(specs):
             for s in specs]
 
 
-def _per_image(specs, fs, form, precision, tile_w=0):
+def _per_image(specs, fs, form, precision):
     outs = []
     for s, f in zip(specs, fs):
         plan = api.GCPlan(s["H"], s["W"], s["sigma_s"], s["sigma_r"], s["N"], form=form, precision=precision,
-                          tile_w=tile_w)
+                          tile_w=s.get("tile_w", 0))
         outs.append(plan.forward(f))
     torch.cuda.synchronize()
     return outs
@@ -49,15 +49,19 @@ SMALL_SPECS = [
 ]
 
 
-@pytest.mark.parametrize("tw", [64, 128, 256])
+@pytest.mark.parametrize("tw", [128, 256])
 @pytest.mark.parametrize("H,W,ss,N,prec", [(300, 517, 10.0, 12, "bf16"), (131, 97, 6.0, 16, "fp16"),
                                            (64, 700, 16.0, 4, "bf16"), (257, 65, 4.0, 20, "bf16")])
 def test_tile_width_does_not_change_the_result(H, W, ss, N, prec, tw):
+    """The shared-memory-Toeplitz row pass gives the same bits at every tile width; the default
+    (tensor-memory Toeplitz) row pass sums the same products in another order."""
     f = torch.from_numpy(synth.edge_smooth_image(H, W, seed=H + W)).to(DEV)
-    ref = api.GCPlan(H, W, ss, 50.0, N, form="fused_tc", precision=prec).forward(f)
+    ref = api.GCPlan(H, W, ss, 50.0, N, form="fused_tc", precision=prec, tile_w=64).forward(f)
     out = api.GCPlan(H, W, ss, 50.0, N, form="fused_tc", precision=prec, tile_w=tw).forward(f)
+    dflt = api.GCPlan(H, W, ss, 50.0, N, form="fused_tc", precision=prec).forward(f)
     torch.cuda.synchronize()
     assert torch.equal(out, ref)
+    assert (dflt - ref).abs().max().item() <= (0.5 if prec == "bf16" else 0.05)
 
 
 @pytest.mark.parametrize("branches", [1, 3, 8])
@@ -82,9 +86,9 @@ def test_batch_equals_per_image_forwards(form, precision, branches):
 
 
 def test_batch_with_mixed_tile_widths_equals_per_image():
-    specs = [dict(s, tile_w=(64, 128, 256)[i % 3]) for i, s in enumerate(SMALL_SPECS)]
+    specs = [dict(s, tile_w=(0, 64, 128, 256)[i % 4]) for i, s in enumerate(SMALL_SPECS)]
     fs = _images(specs)
-    ref = _per_image(SMALL_SPECS, fs, "fused_tc", "bf16")
+    ref = _per_image(specs, fs, "fused_tc", "bf16")
     outs = BT.GCBatch(specs, form="fused_tc", precision="bf16", branches=4).forward(fs)
     torch.cuda.synchronize()
     for o, r in zip(outs, ref):
