@@ -3,6 +3,8 @@
 // operand in shared memory and a chosen tile width; k_tc.cu: column pass + ratio).
 #pragma once
 
+#include <cuda.h>
+
 #include "bfgc_internal.h"
 
 namespace bfgc {
@@ -24,6 +26,7 @@ struct TcGeom {
     // tcgen05 row pass with the Toeplitz operand in tensor memory (k_rows_tc.cu)
     int r_rows;       // padded rows per tile: floor(128 / C) (fewer if the octets do not fit)
     int r_stages;     // channel-buffer ring depth (2 .. 4)
+    int r_stg;        // staging tiles of the drain's TMA stores (1 or 2)
 };
 
 // tw: row-pass tile width (64, 128 or 256; 128 and 256 only for a <= 4), 0 for the default
@@ -34,7 +37,11 @@ size_t umma_smem_bytes(const TcGeom& g);
 int umma_max_octets();
 int rows_tc_max_octets();
 size_t rows_tc_stage_bytes(int a);
+size_t rows_tc_stg_bytes();
 size_t rows_tc_smem_bytes(const TcGeom& g);
+// Tensor map of the row-filtered buffer Y[p][c][x] (3-D: x, c, p) with the given box
+cudaError_t encode_y_map(CUtensorMap* map, void* Y, const TcGeom& g, int C, bool fp16, int box_x, int box_c,
+                         int box_rows, bool swizzle128);
 cudaError_t launch_build_hpass_tc(const float* f, void* Y, const GcParams& p, const Taps& t, const TcGeom& g,
                                   bool fp16, DiagHeader* diag, cudaStream_t s);
 cudaError_t launch_build_hpass_umma(const float* f, void* Y, const GcParams& p, const Taps& t, const TcGeom& g,

@@ -11,86 +11,50 @@
 //   D = 128 lanes (output columns) x 128 fp32 columns (product rows m), one of two
 //     accumulator buffers.
 // 8 + 2a MMAs of 128 x 128 x 16 per tile: 128 + 32a multiply-adds per output and channel.
-// An accumulator lane holds one output column for every (row, channel) pair, so the drain
-// stores each product row of 128 columns straight to Y from registers: neighbouring lanes
-// swap one value (a shuffle) so that every store writes two adjacent BF16/FP16 columns, and
-// a warp's store covers two 64-byte runs of two product rows.
+// An accumulator lane holds one output column for every (row, channel) pair.  Product row m =
+// r C + c of the tile is row p0 C + m of Y viewed as Hp C rows of Wp columns, so the whole
+// tile is one box {128 columns, C channels, TR padded rows} of the 3-D tensor Y[p][c][x]: the
+// drain writes each accumulator column (a product row) into a staging tile [m][x] in shared
+// memory, 2 bytes per lane per instruction (a warp fills 64 contiguous bytes), and one thread
+// stores the tile with a single TMA bulk tensor store.
 //
 // Roles (persistent CTA, one per SM, warp-specialised; the phases of a tile meet at mbarriers
 // only):
-//   warps 8 .. 15 : channel build into an S-stage ring of B buffers (full / empty barriers);
-//                   the f values of the next tile are fetched into registers while waiting;
+//   warps 8 .. 15 : channel build into an S-stage ring of B buffers (full / empty barriers), in
+//                   two groups of four warps that build alternate tiles, so that two tiles are
+//                   built at once (one build thread's power chains are latency-bound); a
+//                   group fetches the f values of its next tile into registers while waiting;
 //   warp 16, one lane : MMA issuer; a tile's MMAs are committed to the stage's empty barrier
 //                   and to the accumulator buffer's full barrier;
-//   warps 0 .. 7  : drain, two per tensor-memory lane quarter, 64 product rows each.
+//   warps 0 .. 7  : drain, two per tensor-memory lane quarter, 64 product rows each, into
+//                   one of NS staging tiles; thread 0 issues the TMA store of the tile.
 // Every mbarrier wait is bounded; a wait that runs out flags the workspace and raises a shared
 // abort flag that ends the other roles' waits, so the kernel always returns.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
+#include <cuda.h>
 
 #include <type_traits>
 
 #include "bfgc_common.cuh"
 #include "bfgc_tc.h"
+#include "bfgc_tcgen05.cuh"
 
 namespace bfgc {
+
+using namespace tc;
 
 namespace {
 
 constexpr int kRDrainWarps = 8;
 constexpr int kRGenWarps = 8;
 constexpr int kRThreads = 32 * (kRDrainWarps + kRGenWarps + 1);
-constexpr int kRGenThreads = 32 * kRGenWarps;
-constexpr int kROctSlots = 3;                     // 8-column octets per build thread per tile
-constexpr unsigned kRWaitNs = 1000000000u;        // bound of one mbarrier wait (1 s)
-constexpr unsigned kRSuspendNs = 20000u;          // suspend-time hint of one try_wait
+constexpr int kRGroupWarps = 4;                   // two build groups: even and odd tiles
+constexpr int kRGroupThreads = 32 * kRGroupWarps;
+constexpr int kROctSlots = 4;                     // 8-column octets per build thread per tile
 constexpr int kRTile = 128;                       // output columns per tile (accumulator lanes)
 constexpr int kRN = 128;                          // product rows per tile (accumulator columns)
 constexpr int kRStageBytesPerKb = kRN * 128;      // one 64-column K-block of B
-
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(su32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" :: "r"(su32(bar)) : "memory");
-}
-// try_wait with a suspend-time hint: a waiting warp sleeps until the phase completes (or the
-// hint runs out) instead of spinning and taking issue slots from the working warps
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok) : "r"(su32(bar)), "r"(parity), "r"(kRSuspendNs) : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-// Wait for the phase of parity `parity` of `bar` (every waiter walks its barrier's phases in
-// order, so the phase before the awaited one is complete).  Gives up when another role raised
-// the abort flag, or (raising it and flagging the workspace) after kRWaitNs.
-__device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, unsigned parity, volatile int* abort_flag,
-                                                DiagHeader* diag) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (global_ns() - t0 > kRWaitNs) break;
-    }
-    *abort_flag = 1;
-    atomicOr(&diag->error_flags, 4u);
-    return false;
-}
-__device__ __forceinline__ void mbar_drain(uint64_t* bar, unsigned parity) {
-    const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(bar, parity) && global_ns() - t0 <= kRWaitNs) {
-    }
-}
+constexpr int kRStgBytes = kRN * kRTile * 2;      // one staging tile [128][128] of 16-bit values
+constexpr unsigned kRFlag = 4u;                   // error flag of this kernel's waits
 
 // Two FP32 lanes in one 64-bit register: packed multiply (one instruction for two products)
 __device__ __forceinline__ uint64_t f2_make(float lo, float hi) {
@@ -107,74 +71,44 @@ __device__ __forceinline__ void f2_split(uint64_t a, float& lo, float& hi) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-
-// FP16 channels are stored times 2^14: |e u^n| <= 1, so the scaled channels and their
-// Gaussian averages stay below 2^14 (FP16 max 65504), while the high powers of mid-range
-// pixels move out of the FP16 subnormal range.  A power of two is exact, and a common
-// factor of every channel cancels in P/Q and in the relative division guard.
-template <typename T> struct kChannelScale { static constexpr float value = 1.0f; };
-template <> struct kChannelScale<__half> { static constexpr float value = 16384.0f; };
-
-template <typename T> __device__ __forceinline__ uint32_t pack2(float lo, float hi);
-template <> __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float lo, float hi) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&v);
-}
-template <> __device__ __forceinline__ uint32_t pack2<__half>(float lo, float hi) {
-    __half2 v = __floats2half2_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&v);
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
-    // load and wait in one statement: the registers are defined only once the wait is done
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-                 "tcgen05.wait::ld.sync.aligned;\n"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-                   "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-                   "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                 : "r"(taddr) : "memory");
-}
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* r) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n"
-                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+// Explicit shared-memory stores (32-bit shared-window addresses), so that no store goes through
+// the generic path
+__device__ __forceinline__ void sts128(uint32_t addr, uint4 w) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n" :: "r"(addr), "r"(w.x), "r"(w.y), "r"(w.z), "r"(w.w)
                  : "memory");
 }
+__device__ __forceinline__ void sts16(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared.b16 [%0], %1;\n" :: "r"(addr), "h"((unsigned short)v) : "memory");
+}
+
+__device__ __forceinline__ void drain_sync() { asm volatile("bar.sync 1, %0;\n" :: "n"(32 * kRDrainWarps) : "memory"); }
 
 }  // namespace
 
-// Shared layout (1024-byte aligned): S stages of KB K-blocks | full[S] | empty[S] | dfull[2] |
-// dempty[2] | TMEM slot | abort flag | last tile committed per accumulator buffer [2].
+// Shared layout (1024-byte aligned): S stages of KB K-blocks | NS staging tiles | full[S] |
+// empty[S] | dfull[2] | dempty[2] | TMEM slot | abort flag | last tile committed per
+// accumulator buffer [2] | drain go flag.
 template <typename T, int A_>
-__global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const float* __restrict__ f, T* __restrict__ Y,
-                                                                 const GcParams p, const Taps t, TcGeom g,
-                                                                 DiagHeader* diag) {
+__global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_constant__ CUtensorMap ymap,
+                                                                 const float* __restrict__ f, const GcParams p,
+                                                                 const Taps t, TcGeom g, DiagHeader* diag) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
     constexpr int a = A_, KIN = kRTile + 32 * A_, KS = KIN / 16, KB = (KIN + 63) / 64, NO = KIN / 8;
     constexpr int ACOLS = KIN / 2;                     // tensor-memory columns of A
     constexpr uint32_t SB = (uint32_t)KB * kRStageBytesPerKb;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int C = p.C, TR = g.r_rows, S = g.r_stages, M = TR * C;
+    const int C = p.C, TR = g.r_rows, S = g.r_stages, NS = g.r_stg, M = TR * C;
     unsigned char* stages = smem;
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * SB);
+    unsigned char* stg = smem + (size_t)S * SB;
+    uint64_t* full = reinterpret_cast<uint64_t*>(stg + (size_t)NS * kRStgBytes);
     uint64_t* empty = full + S;
     uint64_t* dfull = empty + S;
     uint64_t* dempty = dfull + 2;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(dempty + 2);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     volatile int* last_d = abort_flag + 1;
+    volatile int* go = last_d + 2;
     const int tiles_x = (g.Wp + kRTile - 1) / kRTile, tiles_y = (g.Hp + TR - 1) / TR;
     const int ntiles = tiles_x * tiles_y, G = gridDim.x;
     const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;
@@ -186,7 +120,7 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const float* __
     }
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(&full[s], kRGenThreads);
+            mbar_init(&full[s], kRGroupWarps);
             mbar_init(&empty[s], 1);
         }
         for (int d = 0; d < 2; ++d) {
@@ -232,8 +166,9 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const float* __
 
     if (warp >= kRDrainWarps && warp < kRDrainWarps + kRGenWarps) {
         // ------------------------------------------------------------ channel build
-        const int gtid = tid - 32 * kRDrainWarps;
-        const int noct = TR * NO;                      // <= kRGenThreads * kROctSlots (host checks)
+        const int grp = (warp - kRDrainWarps) / kRGroupWarps;              // builds tiles grp, grp + 2, ...
+        const int gtid = tid - 32 * (kRDrainWarps + kRGroupWarps * grp);   // 0 .. kRGroupThreads - 1
+        const int noct = TR * NO;                      // <= kRGroupThreads * kROctSlots (host checks)
         const bool vec = (p.W & 3) == 0;               // 16-byte aligned rows of f
         float fv[kROctSlots][8];
         auto load_f = [&](int tile) {
@@ -241,7 +176,7 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const float* __
             const int p0 = ty * TR, xs0 = tx * kRTile - 16 * a;
 #pragma unroll
             for (int s = 0; s < kROctSlots; ++s) {
-                const int o = gtid + s * kRGenThreads;
+                const int o = gtid + s * kRGroupThreads;
 #pragma unroll
                 for (int e = 0; e < 8; ++e) fv[s][e] = 0.0f;
                 if (tile < ntiles && o < noct) {
@@ -268,16 +203,17 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const float* __
                 }
             }
         };
-        load_f((int)blockIdx.x);
-        for (int it = 0; it < my_tiles; ++it) {
+        // build tile `it` from `fv`, hand it to the MMA issuer, then fetch the group's next tile
+        auto build = [&](int it) -> bool {
             const int s = it % S, use = it / S;
-            if (use > 0 && !mbar_wait_abort(&empty[s], (unsigned)((use - 1) & 1), abort_flag, diag)) break;
+            if (use > 0 && !mbar_wait_abort(&empty[s], (unsigned)((use - 1) & 1), abort_flag, diag, kRFlag))
+                return false;
             unsigned char* B = stages + (size_t)s * SB;
-            // channels e u^c of the fetched octets: 8 independent power chains per octet, one
-            // 16-byte shared store per channel
+            // channels e u^c of the fetched octets: 8 independent power chains per octet (packed
+            // FP32 pairs), one 16-byte shared store per channel
 #pragma unroll
             for (int sl = 0; sl < kROctSlots; ++sl) {
-                const int o = gtid + sl * kRGenThreads;
+                const int o = gtid + sl * kRGroupThreads;
                 if (o >= noct) continue;
                 const int r = o / NO, j = o - r * NO;
                 const int k0 = 8 * j;
@@ -286,7 +222,7 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const float* __
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     u[e] = (fv[sl][e] - p.t_c) * p.inv_sr;
-                    e0[e] = expf(-p.half_mu * u[e] * u[e]) * kChannelScale<T>::value;
+                    e0[e] = expf(-p.half_mu * u[e] * u[e]) * ChannelScale<T>::value;
                 }
                 uint64_t u2[4], v2[4];
 #pragma unroll
@@ -294,8 +230,11 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const float* __
                     u2[e] = f2_make(u[2 * e], u[2 * e + 1]);
                     v2[e] = f2_make(e0[2 * e], e0[2 * e + 1]);
                 }
+                // product row m of a 128-row K-block starts at byte 128 m; its 16-byte chunk
+                // `chunk` sits at chunk ^ (m & 7) (128-byte swizzle)
                 int mrow = r * C;
-                unsigned char* Bk = B + (uint32_t)(k0 >> 6) * kRStageBytesPerKb;
+                const uint32_t Bk = su32(B) + (uint32_t)(k0 >> 6) * kRStageBytesPerKb;
+#pragma unroll 4
                 for (int c = 0; c < C; ++c, ++mrow) {
                     uint4 w;
                     float lo, hi;
@@ -303,15 +242,24 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const float* __
                     f2_split(v2[1], lo, hi); w.y = pack2<T>(lo, hi);
                     f2_split(v2[2], lo, hi); w.z = pack2<T>(lo, hi);
                     f2_split(v2[3], lo, hi); w.w = pack2<T>(lo, hi);
-                    *reinterpret_cast<uint4*>(Bk + (uint32_t)mrow * 128u + (uint32_t)((chunk ^ (mrow & 7)) << 4)) = w;
+                    sts128(Bk + (uint32_t)mrow * 128u + (uint32_t)((chunk ^ (mrow & 7)) << 4), w);
 #pragma unroll
                     for (int e = 0; e < 4; ++e) v2[e] = f2_mul(v2[e], u2[e]);
                 }
             }
+            // one arrive per warp (256 arrives on one barrier would serialise on its word)
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            mbar_arrive(&full[s]);
-            load_f((int)blockIdx.x + (it + 1) * G);
-        }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full[s]);
+            load_f((int)blockIdx.x + (it + 2) * G);
+            return true;
+        };
+        // stage it % S is refilled for tile it after the MMAs of tile it - S; the group's previous
+        // wait (tile it - 2) covered tile it - 2 - S >= it - 2S, so the phase before the awaited
+        // one is complete (S >= 2)
+        load_f((int)blockIdx.x + grp * G);
+        for (int it = grp; it < my_tiles; it += 2)
+            if (!build(it)) break;
     } else if (warp == kRDrainWarps + kRGenWarps) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
@@ -322,8 +270,9 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const float* __
                                    ((uint32_t)(kRTile >> 4) << 24);
             for (int it = 0; it < my_tiles; ++it) {
                 const int s = it % S, use = it / S, d = it & 1, duse = it >> 1;
-                if (!mbar_wait_abort(&full[s], (unsigned)(use & 1), abort_flag, diag)) break;
-                if (duse > 0 && !mbar_wait_abort(&dempty[d], (unsigned)((duse - 1) & 1), abort_flag, diag)) break;
+                if (!mbar_wait_abort(&full[s], (unsigned)(use & 1), abort_flag, diag, kRFlag)) break;
+                if (duse > 0 && !mbar_wait_abort(&dempty[d], (unsigned)((duse - 1) & 1), abort_flag, diag, kRFlag))
+                    break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint64_t b0 = sw128_desc(su32(stages + (size_t)s * SB));
                 const uint32_t dt = tacc + (uint32_t)(d * kRN);
@@ -348,12 +297,19 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const float* __
     } else {
         // ------------------------------------------------------------ drain
         const int q = warp & 3, h = warp >> 2;         // lane quarter, half of the product rows
-        const bool odd = lane & 1;
+        const int x = 32 * q + lane;                   // this lane's column in the tile
         for (int it = 0; it < my_tiles; ++it) {
             const int d = it & 1, duse = it >> 1;
-            bool w = true;
-            if (lane == 0) w = mbar_wait_abort(&dfull[d], (unsigned)(duse & 1), abort_flag, diag);
-            if (!__shfl_sync(0xffffffffu, w, 0)) break;
+            unsigned char* sb = stg + (size_t)(it % NS) * kRStgBytes;
+            // thread 0 waits for the accumulators and for the TMA store that last read this
+            // staging tile, then releases every drain warp (or stops all of them together)
+            if (tid == 0) {
+                if (NS > 1) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+                else asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+                *go = mbar_wait_abort(&dfull[d], (unsigned)(duse & 1), abort_flag, diag, kRFlag) ? 1 : 0;
+            }
+            drain_sync();
+            if (!*go) break;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             uint32_t v0[32], v1[32];
             const uint32_t tl = tacc + ((uint32_t)(32 * q) << 16) + (uint32_t)(d * kRN + 64 * h);
@@ -362,33 +318,38 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const float* __
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&dempty[d]);
-            const int tile = (int)blockIdx.x + it * G;
-            const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
-            const int p0 = ty * TR;
-            // product row m = r C + c of the tile is row p0 C + m of Y (viewed as Hp C rows of
-            // Wp columns); rows from mlim on are padding or past the last padded row
-            const int mlim = min(M, (g.Hp - p0) * C);
-            // this lane's output column; each pair of lanes stores columns xe, xe + 1
-            const int xe = tx * kRTile + 32 * q + (lane & ~1);
-            const bool xok = xe < g.Wp;
-            T* Yb = Y + (size_t)p0 * C * g.Wp + xe;
-            auto store_pairs = [&](const uint32_t* v, int m0) {
+            // staging tile [m][x]: product row m of 128 columns at byte 256 m (rows from M on
+            // are never stored).  Rows m, m + 1 are converted together (one packed conversion,
+            // four times the rate of two single ones) and stored as two 16-bit halves.
+            const uint32_t srow = su32(sb) + (uint32_t)((64 * h) * kRTile + x) * 2u;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    // even lane: product row m0 + 2j, odd lane: m0 + 2j + 1
-                    const float mine = __uint_as_float(odd ? v[2 * j + 1] : v[2 * j]);
-                    const float give = __uint_as_float(odd ? v[2 * j] : v[2 * j + 1]);
-                    const float other = __shfl_xor_sync(0xffffffffu, give, 1);
-                    const int m = m0 + 2 * j + (odd ? 1 : 0);
-                    if (m < mlim && xok) {
-                        const uint32_t w2 = odd ? pack2<T>(other, mine) : pack2<T>(mine, other);
-                        *reinterpret_cast<uint32_t*>(Yb + (size_t)m * g.Wp) = w2;
-                    }
-                }
-            };
-            store_pairs(v0, 64 * h);
-            store_pairs(v1, 64 * h + 32);
+            for (int j = 0; j < 32; j += 2) {
+                const uint32_t w = pack2<T>(__uint_as_float(v0[j]), __uint_as_float(v0[j + 1]));
+                sts16(srow + j * kRTile * 2, w);
+                sts16(srow + (j + 1) * kRTile * 2, w >> 16);
+            }
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+                const uint32_t w = pack2<T>(__uint_as_float(v1[j]), __uint_as_float(v1[j + 1]));
+                sts16(srow + (32 + j) * kRTile * 2, w);
+                sts16(srow + (33 + j) * kRTile * 2, w >> 16);
+            }
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            drain_sync();
+            if (tid == 0) {
+                const int tile = (int)blockIdx.x + it * G;
+                const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+                // box {128 columns, C channels, TR padded rows} at (x0, 0, p0); rows past Hp and
+                // columns past Wp are clipped by the tensor map
+                asm volatile(
+                    "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];\n"
+                    :: "l"(reinterpret_cast<uint64_t>(&ymap)), "r"(tx * kRTile), "r"(0), "r"(ty * TR),
+                       "r"(su32(sb))
+                    : "memory");
+                asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+            }
         }
+        if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
     }
 
     // ---- drain: every MMA committed has completed (immediate unless a wait gave up), then
@@ -397,7 +358,7 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const float* __
     __syncthreads();
     if (tid == 0) {
         for (int d = 0; d < 2; ++d)
-            if (last_d[d] >= 0) mbar_drain(&dfull[d], (unsigned)((last_d[d] >> 1) & 1));
+            if (last_d[d] >= 0) mbar_wait_bounded(&dfull[d], (unsigned)((last_d[d] >> 1) & 1));
     }
     __syncthreads();
     if (warp == kRDrainWarps + kRGenWarps) {
@@ -406,12 +367,15 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const float* __
     }
 }
 
-int rows_tc_max_octets() { return kRGenThreads * kROctSlots; }
+int rows_tc_max_octets() { return kRGroupThreads * kROctSlots; }
 
 size_t rows_tc_stage_bytes(int a) { return (size_t)((kRTile + 32 * a + 63) / 64) * kRStageBytesPerKb; }
 
+size_t rows_tc_stg_bytes() { return kRStgBytes; }
+
 size_t rows_tc_smem_bytes(const TcGeom& g) {
-    return (size_t)g.r_stages * rows_tc_stage_bytes(g.a) + (2 * g.r_stages + 4) * 8 + 16 + 1024;
+    return (size_t)g.r_stages * rows_tc_stage_bytes(g.a) + (size_t)g.r_stg * kRStgBytes + (2 * g.r_stages + 4) * 8 +
+           32 + 1024;
 }
 
 template <typename T, int A_>
@@ -421,12 +385,16 @@ cudaError_t launch_rows_impl(const float* f, void* Y, const GcParams& p, const T
     auto kern = k_build_hpass_tc<T, A_>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // the store box of one tile: 128 columns x C channels x TR padded rows, no swizzle
+    alignas(64) CUtensorMap map;
+    e = encode_y_map(&map, Y, g, p.C, std::is_same<T, __half>::value, kRTile, p.C, g.r_rows, false);
+    if (e != cudaSuccess) return e;
     const int tiles = ((g.Wp + kRTile - 1) / kRTile) * ((g.Hp + g.r_rows - 1) / g.r_rows);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::max(1, std::min(tiles, sms));
-    kern<<<grid, kRThreads, smem, s>>>(f, static_cast<T*>(Y), p, t, g, diag);
+    kern<<<grid, kRThreads, smem, s>>>(map, f, p, t, g, diag);
     return cudaGetLastError();
 }
 

@@ -47,8 +47,11 @@
 
 #include "bfgc_common.cuh"
 #include "bfgc_tc.h"
+#include "bfgc_tcgen05.cuh"
 
 namespace bfgc {
+
+using namespace tc;
 
 namespace {
 
@@ -56,92 +59,13 @@ constexpr int VR = 128;                          // output rows per tile (tensor
 constexpr int VC = 64;                           // output columns per tile (MMA N)
 constexpr int kEpiWarps = 16;                    // 4 per tensor-memory lane quarter
 constexpr int kVThreads = 32 * (kEpiWarps + 3);
-constexpr unsigned kVSpin = 1u << 22;            // polls per bounded mbarrier wait
+constexpr unsigned kVFlag = 1u;                  // error flag of this kernel's waits
 
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(su32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" :: "r"(su32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" :: "r"(su32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok) : "r"(su32(bar)), "r"(parity) : "memory");
-    return ok != 0;
-}
-// Wait for phase `parity` of `bar`.  Gives up when another role raised the abort flag, or
-// (raising it, and flagging the workspace) when the bounded spin runs out.  (mbarrier waits go
-// by phase parity: every waiter below walks its barrier's phases in order, so the phase before
-// the awaited one is always complete.)
-__device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, unsigned parity, volatile int* abort_flag,
-                                                DiagHeader* diag) {
-    for (unsigned i = 0; i < kVSpin; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 31) == 31 && *abort_flag) return false;
-    }
-    *abort_flag = 1;
-    atomicOr(&diag->error_flags, 1u);
-    return false;
-}
-// Bounded wait without abort, for draining asynchronous work before the CTA exits.
-__device__ __forceinline__ void mbar_drain(uint64_t* bar, unsigned parity) {
-    for (unsigned i = 0; i < kVSpin; ++i)
-        if (mbar_try_wait(bar, parity)) return;
-}
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int c, int y, uint64_t* bar) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n"
         :: "r"(su32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(c), "r"(y), "r"(su32(bar))
         : "memory");
-}
-
-// Shared-memory matrix descriptor with the 128-byte swizzle: start address, leading and
-// stride byte offsets (>> 4), descriptor version 1 (bit 46), swizzle mode 2 (bits 61..63).
-// MN-major operand with 64 elements per line: 8-line (K) groups 1024 bytes apart (SBO),
-// 64-element MN blocks LBO apart (one block here).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr, uint32_t lbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-
-template <typename T> __device__ __forceinline__ uint32_t pack2(float lo, float hi);
-template <> __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float lo, float hi) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&v);
-}
-template <> __device__ __forceinline__ uint32_t pack2<__half>(float lo, float hi) {
-    __half2 v = __floats2half2_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&v);
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* z) {
-    uint32_t v[16];
-    // load and wait in one statement: the registers are defined only once the wait is done
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-                 "tcgen05.wait::ld.sync.aligned;\n"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                 : "r"(taddr) : "memory");
-#pragma unroll
-    for (int j = 0; j < 16; ++j) z[j] = __uint_as_float(v[j]);
-}
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* r) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n"
-                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
-                 : "memory");
 }
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
@@ -244,7 +168,8 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
                 const int it = k / C, i = k - it * C, s = stage_of(k), use = (k >> 1) / S2;
                 const int tile = (int)blockIdx.x + it * G;
                 const int x0 = (tile / tiles_y) * VC, y0 = (tile % tiles_y) * VR;
-                if (use > 0 && !mbar_wait_abort(&empty[s], (unsigned)((use - 1) & 1), abort_flag, diag)) break;
+                if (use > 0 && !mbar_wait_abort(&empty[s], (unsigned)((use - 1) & 1), abort_flag, diag, kVFlag))
+                    break;
                 stage_k[s] = k;
                 mbar_expect_tx(&full[s], (unsigned)SB);
                 // padded rows y0 .. y0 + RIN of channel C-1-i (highest channel first)
@@ -264,8 +189,9 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
             for (int j = warp - kEpiWarps - 1; j < total; j += 2) {
                 const int s = stage_of(j), b = buf_of(j);
                 const int suse = (j >> 1) / S2, buse = (j >> 1) / NB2;
-                if (!mbar_wait_abort(&full[s], (unsigned)(suse & 1), abort_flag, diag)) break;
-                if (buse > 0 && !mbar_wait_abort(&tempty[b], (unsigned)((buse - 1) & 1), abort_flag, diag)) break;
+                if (!mbar_wait_abort(&full[s], (unsigned)(suse & 1), abort_flag, diag, kVFlag)) break;
+                if (buse > 0 && !mbar_wait_abort(&tempty[b], (unsigned)((buse - 1) & 1), abort_flag, diag, kVFlag))
+                    break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint64_t b0 = sw128_desc(su32(stages + (size_t)s * SB), SB);
                 const uint32_t d = tacc + (uint32_t)(b * VC);
@@ -340,7 +266,7 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
             for (int i = 0; i < C && ok; ++i, ++gi) {
                 const int b = buf_of(gi), m = C - 1 - i;
                 bool w = true;
-                if (lane == 0) w = mbar_wait_abort(&tfull[b], (unsigned)(((gi >> 1) / NB2) & 1), abort_flag, diag);
+                if (lane == 0) w = mbar_wait_abort(&tfull[b], (unsigned)(((gi >> 1) / NB2) & 1), abort_flag, diag, kVFlag);
                 ok = __shfl_sync(0xffffffffu, w, 0);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -400,9 +326,9 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
     __syncthreads();
     if (tid == 0) {
         for (int s = 0; s < S; ++s)
-            if (stage_k[s] >= 0) mbar_drain(&full[s], (unsigned)(((stage_k[s] >> 1) / S2) & 1));
+            if (stage_k[s] >= 0) mbar_wait_bounded(&full[s], (unsigned)(((stage_k[s] >> 1) / S2) & 1));
         for (int b = 0; b < NB; ++b)
-            if (buf_j[b] >= 0) mbar_drain(&tfull[b], (unsigned)(((buf_j[b] >> 1) / NB2) & 1));
+            if (buf_j[b] >= 0) mbar_wait_bounded(&tfull[b], (unsigned)(((buf_j[b] >> 1) / NB2) & 1));
     }
     __syncthreads();
     if (warp == kEpiWarps) {
@@ -440,22 +366,13 @@ size_t vu_smem_bytes(const TcGeom& g) {
 template <typename T, int A>
 cudaError_t launch_vpass_impl(const float* f, void* Yv, float* out, const GcParams& p, const Taps& t,
                               const TcGeom& g, DiagHeader* diag, cudaStream_t s) {
-    EncodeTiledFn enc = encode_fn();
-    if (!enc) return cudaErrorNotSupported;
-    // Y[p][c][x] as a 3-D tensor: x (Wp), c (C), p (Hp); one box = 64 columns x 1 channel x rows
+    // one box = 64 columns x 1 channel x kb_box_rows padded rows, 128-byte swizzle
     alignas(64) CUtensorMap map;
-    const cuuint64_t dims[3] = {(cuuint64_t)g.Wp, (cuuint64_t)p.C, (cuuint64_t)g.Hp};
-    const cuuint64_t strides[2] = {(cuuint64_t)g.Wp * sizeof(T), (cuuint64_t)p.C * g.Wp * sizeof(T)};
-    const cuuint32_t box[3] = {(cuuint32_t)VC, 1u, (cuuint32_t)g.kb_box_rows};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(&map, std::is_same<T, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                                          : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
-                     3, Yv, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    cudaError_t e = encode_y_map(&map, Yv, g, p.C, std::is_same<T, __half>::value, VC, 1, g.kb_box_rows, true);
+    if (e != cudaSuccess) return e;
     const size_t smem = vu_smem_bytes(g);
     auto kern = k_vpass_combine_umma<T, A>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -484,6 +401,22 @@ cudaError_t launch_vpass_a(const float* f, void* Y, float* out, const GcParams& 
 
 }  // namespace
 
+cudaError_t encode_y_map(CUtensorMap* map, void* Y, const TcGeom& g, int C, bool fp16, int box_x, int box_c,
+                         int box_rows, bool swizzle128) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    // Y[p][c][x] as a 3-D tensor: x (Wp), c (C), p (Hp)
+    const cuuint64_t dims[3] = {(cuuint64_t)g.Wp, (cuuint64_t)C, (cuuint64_t)g.Hp};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.Wp * 2, (cuuint64_t)C * g.Wp * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_c, (cuuint32_t)box_rows};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(map, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, Y, dims,
+                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 TcGeom tc_geometry(int H, int W, int R, int C, int tw) {
     TcGeom g{};
     g.a = (R + 15) / 16;
@@ -505,7 +438,16 @@ TcGeom tc_geometry(int H, int W, int R, int C, int tw) {
     g.u_nkb = g.u_tw / 64 + 2 * g.u_hb;
     g.u_kbb = (64 + 32 * g.a + 63) / 64;
     g.r_rows = std::max(1, std::min(128 / std::max(1, C), rows_tc_max_octets() / ((128 + 32 * g.a) / 8)));
-    g.r_stages = (int)std::min<size_t>(4, (size_t)(200 * 1024) / rows_tc_stage_bytes(g.a));
+    // ring depth and staging tiles of the tensor-memory row pass within 224 KB of shared memory
+    static const int kChoices[6][2] = {{4, 2}, {3, 2}, {4, 1}, {3, 1}, {2, 2}, {2, 1}};
+    g.r_stages = 0;
+    g.r_stg = 0;
+    for (const auto& c : kChoices)
+        if ((size_t)c[0] * rows_tc_stage_bytes(g.a) + (size_t)c[1] * rows_tc_stg_bytes() <= 224 * 1024) {
+            g.r_stages = c[0];
+            g.r_stg = c[1];
+            break;
+        }
     return g;
 }
 
