@@ -20,11 +20,11 @@
 //
 // Roles (persistent CTA, one per SM, warp-specialised; the phases of a tile meet at mbarriers
 // only):
-//   warps 8 .. 15 : channel build into an S-stage ring of B buffers (full / empty barriers), in
-//                   two groups of four warps that build alternate tiles, so that two tiles are
-//                   built at once (one build thread's power chains are latency-bound); a
-//                   group fetches the f values of its next tile into registers while waiting;
-//   warp 16, one lane : MMA issuer; a tile's MMAs are committed to the stage's empty barrier
+//   warps 8 .. 19 : channel build into an S-stage ring of B buffers (full / empty barriers), in
+//                   NG = min(3, S) groups of four warps that take the tiles in turn, so that NG
+//                   tiles are built at once (one build thread's power chains are latency-bound);
+//                   a group fetches the f values of its next tile into registers while waiting;
+//   warp 20, one lane : MMA issuer; a tile's MMAs are committed to the stage's empty barrier
 //                   and to the accumulator buffer's full barrier;
 //   warps 0 .. 7  : drain, two per tensor-memory lane quarter, 64 product rows each, into
 //                   one of NS staging tiles; thread 0 issues the TMA store of the tile.
@@ -45,9 +45,10 @@ using namespace tc;
 namespace {
 
 constexpr int kRDrainWarps = 8;
-constexpr int kRGenWarps = 8;
+constexpr int kRGenWarps = 12;
 constexpr int kRThreads = 32 * (kRDrainWarps + kRGenWarps + 1);
-constexpr int kRGroupWarps = 4;                   // two build groups: even and odd tiles
+constexpr int kRGroupWarps = 4;                   // build groups of four warps (up to three)
+constexpr int kRGroups = kRGenWarps / kRGroupWarps;
 constexpr int kRGroupThreads = 32 * kRGroupWarps;
 constexpr int kROctSlots = 4;                     // 8-column octets per build thread per tile
 constexpr int kRTile = 128;                       // output columns per tile (accumulator lanes)
@@ -55,21 +56,6 @@ constexpr int kRN = 128;                          // product rows per tile (accu
 constexpr int kRStageBytesPerKb = kRN * 128;      // one 64-column K-block of B
 constexpr int kRStgBytes = kRN * kRTile * 2;      // one staging tile [128][128] of 16-bit values
 constexpr unsigned kRFlag = 4u;                   // error flag of this kernel's waits
-
-// Two FP32 lanes in one 64-bit register: packed multiply (one instruction for two products)
-__device__ __forceinline__ uint64_t f2_make(float lo, float hi) {
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
-    uint64_t r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ void f2_split(uint64_t a, float& lo, float& hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
-}
 
 // Explicit shared-memory stores (32-bit shared-window addresses), so that no store goes through
 // the generic path
@@ -166,7 +152,8 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
 
     if (warp >= kRDrainWarps && warp < kRDrainWarps + kRGenWarps) {
         // ------------------------------------------------------------ channel build
-        const int grp = (warp - kRDrainWarps) / kRGroupWarps;              // builds tiles grp, grp + 2, ...
+        const int NG = min(kRGroups, S);               // active build groups
+        const int grp = (warp - kRDrainWarps) / kRGroupWarps;              // builds tiles grp, grp + NG, ...
         const int gtid = tid - 32 * (kRDrainWarps + kRGroupWarps * grp);   // 0 .. kRGroupThreads - 1
         const int noct = TR * NO;                      // <= kRGroupThreads * kROctSlots (host checks)
         const bool vec = (p.W & 3) == 0;               // 16-byte aligned rows of f
@@ -251,15 +238,17 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&full[s]);
-            load_f((int)blockIdx.x + (it + 2) * G);
+            load_f((int)blockIdx.x + (it + NG) * G);
             return true;
         };
         // stage it % S is refilled for tile it after the MMAs of tile it - S; the group's previous
-        // wait (tile it - 2) covered tile it - 2 - S >= it - 2S, so the phase before the awaited
-        // one is complete (S >= 2)
-        load_f((int)blockIdx.x + grp * G);
-        for (int it = grp; it < my_tiles; it += 2)
-            if (!build(it)) break;
+        // wait (tile it - NG) covered tile it - NG - S >= it - 2S, so the phase before the awaited
+        // one is complete (NG <= S)
+        if (grp < NG) {
+            load_f((int)blockIdx.x + grp * G);
+            for (int it = grp; it < my_tiles; it += NG)
+                if (!build(it)) break;
+        }
     } else if (warp == kRDrainWarps + kRGenWarps) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
