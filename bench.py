@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--forms", default=None, help="comma list of form:precision to run")
     ap.add_argument("--size", default=None, help="HxW instead of 2160x3840 (profiling cases)")
-    ap.add_argument("--study", default=None, choices=["precision", "gpf", "batch"],
+    ap.add_argument("--study", default=None, choices=["precision", "gpf", "batch", "sigma"],
                     help="instead of the benchmark: the 8192x8192 precision sweep, the GPF/GCF table at 4K, "
                          "or the uneven 256-image batch")
     ap.add_argument("--batch-count", type=int, default=256, help="images of the batch study")
@@ -396,6 +396,9 @@ def run_study(args):
     if args.study == "batch":
         run_batch_study(args, dev)
         return
+    if args.study == "sigma":
+        run_sigma_study(args, dev)
+        return
     if args.study == "gpf":
         f = synth.workload("uhd")["f"]
         ft = torch.from_numpy(f).to(dev)
@@ -443,6 +446,47 @@ def run_study(args):
                     "n_guarded": d["n_guarded"], "error_flags": d["error_flags"]}), flush=True)
                 del plan, ws, out
                 torch.cuda.empty_cache()
+
+
+def run_sigma_study(args, dev):
+    """The 4K benchmark image at sigma_r = 50, N = 20 over sigma_s in {5, 10, 16, 20, 24, 32, 42,
+    50, 64}: ms per image of the plain (FP32), recursive (FP32) and tensor-core (BF16; R <= 128)
+    forms (CUDA events, 5 runs after 2 warm-ups) and their PSNR against the exact filter
+    (bf_direct).  This is where the recursive form's O(1) cost in sigma_s overtakes the others."""
+    import numpy as np
+    import torch
+    from paper_1605_02178_gb300 import api, bfgc, synth
+
+    def psnr(a, b):
+        mse = float(np.mean((a - b) ** 2))
+        return float("inf") if mse == 0.0 else 10.0 * math.log10(255.0 ** 2 / mse)
+    f = synth.workload("uhd")["f"]
+    ft = torch.from_numpy(f).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    for ss in (5.0, 10.0, 16.0, 20.0, 24.0, 32.0, 42.0, 50.0, 64.0):
+        exact = bfgc.bf_direct(ft, ss, 50.0).cpu().numpy().astype(np.float64)
+        row = {"study": "sigma", "image": "uhd 3840x2160", "sigma_s": ss, "sigma_r": 50.0, "N": 20,
+               "R": int(math.ceil(3.0 * ss - 1e-9))}
+        for form, prec in (("plain", "fp32"), ("recursive", "fp32"), ("fused_tc", "bf16")):
+            try:
+                plan = api.GCPlan(2160, 3840, ss, 50.0, 20, form=form, precision=prec)
+                ws = plan.workspace("fwd", dev)
+            except bfgc.BfError:
+                row[form] = None
+                continue
+            out = torch.empty_like(ft)
+            for _ in range(2):
+                plan.forward(ft, out, ws, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(5):
+                plan.forward(ft, out, ws, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            row[form] = {"ms": e0.elapsed_time(e1) / 5,
+                         "psnr_vs_exact_db": psnr(out.cpu().numpy().astype(np.float64), exact)}
+            del plan, ws, out
+        print(json.dumps(row), flush=True)
 
 
 def run_batch_study(args, dev):

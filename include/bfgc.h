@@ -70,8 +70,19 @@ enum {
     BF_FORM_FUSED_TC = 1,     /* 2 kernels: (build + row filter) and (column filter + ratio), the
                                  spatial Gaussian as a banded Toeplitz product on tensor cores;
                                  channels stored as BF16 or FP16, FP32 accumulation */
-    BF_FORM_RECURSIVE = 2     /* recursive (IIR) stand-in for eq. (7), Young-van Vliet 1995 */
+    BF_FORM_RECURSIVE = 2,    /* recursive (IIR) stand-in for eq. (7), Young-van Vliet 1995 */
+    BF_FORM_AUTO = 3          /* chosen from R and the precision, and re-chosen when the precision
+                                 changes (bf_gc_plan_info reports the choice): with BF16 / FP16
+                                 storage the tensor-core form while R <= 128 (its limit), else the
+                                 recursive form; with FP32 the plain form while R <= BF_AUTO_PLAIN_MAX_R,
+                                 else the recursive form (whose cost does not grow with sigma_s;
+                                 it approximates the Gaussian of eq. (7), 57-65 dB PSNR against the
+                                 exact filter on 4K test images, instead of computing it exactly) */
 };
+/* Largest window radius for which BF_FORM_AUTO keeps the plain form at FP32: on a GB300 the
+ * plain form costs about 1.9 ms + 0.034 ms per unit of R per 4K image (N = 20), the recursive
+ * form about 4.1 ms whatever R; they cross near R = 72 (sigma_s = 24). */
+#define BF_AUTO_PLAIN_MAX_R 72
 enum { BF_PREC_FP32 = 0, BF_PREC_BF16 = 1, BF_PREC_FP16 = 2 };
 enum {
     BF_POLY_CHEBYSHEV = 0,    /* c_n of eq. (19): Gauss-Chebyshev filter (GCF)          */

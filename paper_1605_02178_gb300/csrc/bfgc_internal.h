@@ -62,6 +62,7 @@ struct bf_gc_plan_s {
     int H, W, N, R, C;
     double sigma_s, sigma_r, L, U;
     int form, precision, poly, save_channels, tile_w;
+    bool form_auto;      // BF_FORM_AUTO was asked for: `form` is re-chosen on precision changes
     bool used;
     // derived (refit on option change)
     double t_c, s_r, mu, kappa, fit_err;

@@ -171,6 +171,13 @@ size_t bwd_workspace(const bf_gc_plan_s* p) {
     return BF_WS_HEADER + (2 * (size_t)p->C + 1) * cs * sizeof(float) + 2 * bfgc::kAdjBlocks * sizeof(double);
 }
 
+// BF_FORM_AUTO: the tensor-core form with 16-bit storage while it exists (R <= 128), the plain
+// form at FP32 up to the measured crossover, the recursive form beyond either
+int auto_form(const bf_gc_plan_s* p) {
+    if (p->precision != BF_PREC_FP32) return bfgc::tc_supported(p->R, p->C) ? BF_FORM_FUSED_TC : BF_FORM_RECURSIVE;
+    return p->R <= BF_AUTO_PLAIN_MAX_R ? BF_FORM_PLAIN : BF_FORM_RECURSIVE;
+}
+
 bool form_supported(const bf_gc_plan_s* p) {
     switch (p->form) {
     case BF_FORM_PLAIN:
@@ -178,7 +185,8 @@ bool form_supported(const bf_gc_plan_s* p) {
     case BF_FORM_FUSED_TC:
         return (p->precision == BF_PREC_BF16 || p->precision == BF_PREC_FP16) && bfgc::tc_supported(p->R, p->C);
     case BF_FORM_RECURSIVE:
-        return p->precision == BF_PREC_FP32 && p->sigma_s >= 0.5;
+        // computed in FP32; chosen by BF_FORM_AUTO also when 16-bit storage was allowed
+        return (p->precision == BF_PREC_FP32 || p->form_auto) && p->sigma_s >= 0.5;
     default:
         return false;
     }
@@ -236,7 +244,7 @@ bf_status bf_gc_plan(int H, int W, double sigma_s, double sigma_r, int N, bf_gc_
     p->H = H; p->W = W; p->N = N; p->C = N + 2; p->R = R;
     p->sigma_s = sigma_s; p->sigma_r = sigma_r;
     p->L = 0.0; p->U = 255.0;
-    p->form = BF_FORM_PLAIN; p->precision = BF_PREC_FP32; p->poly = BF_POLY_CHEBYSHEV;
+    p->form = BF_FORM_PLAIN; p->precision = BF_PREC_FP32; p->poly = BF_POLY_CHEBYSHEV; p->form_auto = false;
     p->save_channels = 0; p->tile_w = 0; p->used = false;
     refit(p);
     make_taps(sigma_s, R, &p->taps);
@@ -249,12 +257,14 @@ bf_status bf_gc_plan_set(bf_gc_plan_t p, int option, double value) {
     const int iv = (int)value;
     switch (option) {
     case BF_OPT_FORM:
-        if (iv != value || iv < BF_FORM_PLAIN || iv > BF_FORM_RECURSIVE) return BF_ERR_INVALID_ARG;
-        p->form = iv;
+        if (iv != value || iv < BF_FORM_PLAIN || iv > BF_FORM_AUTO) return BF_ERR_INVALID_ARG;
+        p->form_auto = iv == BF_FORM_AUTO;
+        p->form = p->form_auto ? auto_form(p) : iv;
         return BF_OK;
     case BF_OPT_PRECISION:
         if (iv != value || iv < BF_PREC_FP32 || iv > BF_PREC_FP16) return BF_ERR_INVALID_ARG;
         p->precision = iv;
+        if (p->form_auto) p->form = auto_form(p);
         return BF_OK;
     case BF_OPT_RANGE_L:
     case BF_OPT_RANGE_U: {
