@@ -67,6 +67,27 @@ __device__ __forceinline__ void sts16(uint32_t addr, uint32_t v) {
     asm volatile("st.shared.b16 [%0], %1;\n" :: "r"(addr), "h"((unsigned short)v) : "memory");
 }
 
+// 16 lanes x 64 columns of tensor memory, in the fragment layout of 16x256b: thread t holds
+// lane t/4 (r[4i], r[4i+1]) and lane t/4 + 8 (r[4i+2], r[4i+3]) at columns 8i + 2(t%4) and
+// 8i + 2(t%4) + 1, i = 0 .. 7
+__device__ __forceinline__ void tmem_ld_16x256b_x8(uint32_t taddr, uint32_t* v) {
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                 "tcgen05.wait::ld.sync.aligned;\n"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+                   "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+                   "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                 : "r"(taddr) : "memory");
+}
+// Four 8x8 matrices of 16-bit values, stored transposed: smem row i of matrix k (address from
+// thread 8k + i) receives column i of the matrix whose row t/4, columns 2(t%4), 2(t%4) + 1 are
+// in register k of thread t
+__device__ __forceinline__ void stmatrix_x4_trans(uint32_t addr, uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3) {
+    asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1, %2, %3, %4};\n"
+                 :: "r"(addr), "r"(r0), "r"(r1), "r"(r2), "r"(r3) : "memory");
+}
+
 __device__ __forceinline__ void drain_sync() { asm volatile("bar.sync 1, %0;\n" :: "n"(32 * kRDrainWarps) : "memory"); }
 
 }  // namespace
@@ -286,7 +307,12 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
     } else {
         // ------------------------------------------------------------ drain
         const int q = warp & 3, h = warp >> 2;         // lane quarter, half of the product rows
-        const int x = 32 * q + lane;                   // this lane's column in the tile
+        // stmatrix row address of this thread: matrix k = lane / 8 covers the 8 columns
+        // x = 32q + 16L + 8 (k & 1) .. + 7 and the 8 product rows 64h + 8(i + (k >> 1)) .. + 7
+        // of column block pair i; row i8 = lane % 8 of it is 16 bytes of [m][x] in the staging
+        // half x / 64 (64 columns, 128-byte rows, 128-byte swizzle: chunk j of row m at
+        // j ^ (m & 7))
+        const int mk = lane >> 3, mr = lane & 7;
         for (int it = 0; it < my_tiles; ++it) {
             const int d = it & 1, duse = it >> 1;
             unsigned char* sb = stg + (size_t)(it % NS) * kRStgBytes;
@@ -300,41 +326,51 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
             drain_sync();
             if (!*go) break;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            // lanes 32q .. 32q + 15 (L = 0) and 32q + 16 .. 32q + 31 (L = 1), columns 64h .. 64h + 63
             uint32_t v0[32], v1[32];
             const uint32_t tl = tacc + ((uint32_t)(32 * q) << 16) + (uint32_t)(d * kRN + 64 * h);
-            tmem_ld32(tl, v0);
-            tmem_ld32(tl + 32u, v1);
+            tmem_ld_16x256b_x8(tl, v0);
+            tmem_ld_16x256b_x8(tl + (16u << 16), v1);
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&dempty[d]);
-            // staging tile [m][x]: product row m of 128 columns at byte 256 m (rows from M on
-            // are never stored).  Rows m, m + 1 are converted together (one packed conversion,
-            // four times the rate of two single ones) and stored as two 16-bit halves.
-            const uint32_t srow = su32(sb) + (uint32_t)((64 * h) * kRTile + x) * 2u;
+            // product rows m, m + 1 of one column x in one packed conversion; stmatrix with
+            // transpose turns the fragments into 16-byte runs of 8 columns of one product row
+            // (rows from M on are never stored)
+            auto stage = [&](const uint32_t* v, int L) {
+                const int xb = 32 * q + 16 * L + 8 * (mk & 1);       // first column of matrix mk
+                const uint32_t half = su32(sb) + (uint32_t)(xb >> 6) * (kRStgBytes / 2);
+                const int j = (xb & 63) >> 3;
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-                const uint32_t w = pack2<T>(__uint_as_float(v0[j]), __uint_as_float(v0[j + 1]));
-                sts16(srow + j * kRTile * 2, w);
-                sts16(srow + (j + 1) * kRTile * 2, w >> 16);
-            }
-#pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-                const uint32_t w = pack2<T>(__uint_as_float(v1[j]), __uint_as_float(v1[j + 1]));
-                sts16(srow + (32 + j) * kRTile * 2, w);
-                sts16(srow + (33 + j) * kRTile * 2, w >> 16);
-            }
+                for (int i = 0; i < 8; i += 2) {
+                    const int m = 64 * h + 8 * (i + (mk >> 1)) + mr;
+                    const uint32_t addr = half + (uint32_t)m * 128u + (uint32_t)((j ^ (m & 7)) << 4);
+                    stmatrix_x4_trans(addr,
+                                      pack2<T>(__uint_as_float(v[4 * i]), __uint_as_float(v[4 * i + 1])),
+                                      pack2<T>(__uint_as_float(v[4 * i + 2]), __uint_as_float(v[4 * i + 3])),
+                                      pack2<T>(__uint_as_float(v[4 * i + 4]), __uint_as_float(v[4 * i + 5])),
+                                      pack2<T>(__uint_as_float(v[4 * i + 6]), __uint_as_float(v[4 * i + 7])));
+                }
+            };
+            stage(v0, 0);
+            stage(v1, 1);
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             drain_sync();
             if (tid == 0) {
                 const int tile = (int)blockIdx.x + it * G;
                 const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
-                // box {128 columns, C channels, TR padded rows} at (x0, 0, p0); rows past Hp and
-                // columns past Wp are clipped by the tensor map
-                asm volatile(
-                    "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];\n"
-                    :: "l"(reinterpret_cast<uint64_t>(&ymap)), "r"(tx * kRTile), "r"(0), "r"(ty * TR),
-                       "r"(su32(sb))
-                    : "memory");
+                // two boxes {64 columns, C channels, TR padded rows} at (x0 + 64 half, 0, p0), from
+                // the two 128-byte-swizzled staging halves; rows past Hp and columns past Wp are
+                // clipped by the tensor map, and a half that starts at or past Wp is skipped
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int xs = tx * kRTile + 64 * hh;
+                    if (xs >= g.Wp) break;
+                    asm volatile(
+                        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];\n"
+                        :: "l"(reinterpret_cast<uint64_t>(&ymap)), "r"(xs), "r"(0), "r"(ty * TR),
+                           "r"(su32(sb) + (uint32_t)hh * (kRStgBytes / 2))
+                        : "memory");
+                }
                 asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
             }
         }
@@ -374,9 +410,9 @@ cudaError_t launch_rows_impl(const float* f, void* Y, const GcParams& p, const T
     auto kern = k_build_hpass_tc<T, A_>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    // the store box of one tile: 128 columns x C channels x TR padded rows, no swizzle
+    // the store box of half a tile: 64 columns x C channels x TR padded rows, 128-byte swizzle
     alignas(64) CUtensorMap map;
-    e = encode_y_map(&map, Y, g, p.C, std::is_same<T, __half>::value, kRTile, p.C, g.r_rows, false);
+    e = encode_y_map(&map, Y, g, p.C, std::is_same<T, __half>::value, kRTile / 2, p.C, g.r_rows, true);
     if (e != cudaSuccess) return e;
     const int tiles = ((g.Wp + kRTile - 1) / kRTile) * ((g.Hp + g.r_rows - 1) / g.r_rows);
     int dev = 0, sms = 0;
