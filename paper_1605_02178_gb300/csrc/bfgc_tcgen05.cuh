@@ -34,6 +34,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
         : "=r"(ok) : "r"(su32(bar)), "r"(parity), "r"(kSuspendNs) : "memory");
     return ok != 0;
 }
+// try_wait without a suspend hint (returns at once): for waits on the critical path, where a
+// sleeping warp would add its wake-up latency to every hand-off
+__device__ __forceinline__ bool mbar_poll(uint64_t* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(su32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -51,6 +60,22 @@ __device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, unsigned parity, 
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
         if (global_ns() - t0 > kWaitNs) break;
+    }
+    *abort_flag = 1;
+    atomicOr(&diag->error_flags, flag);
+    return false;
+}
+// As mbar_wait_abort, polling without the suspend hint
+__device__ __forceinline__ bool mbar_wait_abort_poll(uint64_t* bar, unsigned parity, volatile int* abort_flag,
+                                                     DiagHeader* diag, unsigned flag) {
+    if (mbar_poll(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (unsigned i = 0;; ++i) {
+        if (mbar_poll(bar, parity)) return true;
+        if ((i & 15) == 15) {
+            if (*abort_flag) return false;
+            if (global_ns() - t0 > kWaitNs) break;
+        }
     }
     *abort_flag = 1;
     atomicOr(&diag->error_flags, flag);

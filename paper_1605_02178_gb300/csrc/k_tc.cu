@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
             for (int i = 0; i < C && ok; ++i, ++gi) {
                 const int b = buf_of(gi), m = C - 1 - i;
                 bool w = true;
-                if (lane == 0) w = mbar_wait_abort(&tfull[b], (unsigned)(((gi >> 1) / NB2) & 1), abort_flag, diag, kVFlag);
+                if (lane == 0) w = mbar_wait_abort_poll(&tfull[b], (unsigned)(((gi >> 1) / NB2) & 1), abort_flag, diag, kVFlag);
                 ok = __shfl_sync(0xffffffffu, w, 0);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
