@@ -243,6 +243,10 @@ bf_status bf_direct(int H, int W, double sigma_s, double sigma_r, const float *d
 const char *bf_status_string(bf_status s);
 const char *bf_version(void);
 
+/* The CUDA error code behind the last BF_ERR_CUDA returned to this thread (0 if none), and in
+ * *name (may be NULL) its name as a static string.  Host only. */
+int bf_last_cuda_error(const char **name);
+
 #ifdef __cplusplus
 }
 #endif

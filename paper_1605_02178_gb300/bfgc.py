@@ -70,6 +70,7 @@ SIGNATURES = {
     "bf_direct": (_I, [_I, _I, _D, _D, _P, _P, _P]),
     "bf_status_string": (ctypes.c_char_p, [_I]),
     "bf_version": (ctypes.c_char_p, []),
+    "bf_last_cuda_error": (_I, [ctypes.POINTER(ctypes.c_char_p)]),
 }
 
 _lib = None
@@ -97,6 +98,9 @@ def lib():
 class BfError(RuntimeError):
     def __init__(self, status, what):
         msg = lib().bf_status_string(status).decode()
+        if status == BF_ERR_CUDA:
+            code, name = bf_last_cuda_error()
+            msg += f" [{name} ({code})]"
         super().__init__(f"{what}: {msg} (status {status})")
         self.status = status
 
@@ -258,3 +262,10 @@ def bf_status_string(status):
 
 def bf_version():
     return lib().bf_version().decode()
+
+
+def bf_last_cuda_error():
+    """(code, name) of the CUDA error behind the last BF_ERR_CUDA of this thread."""
+    name = ctypes.c_char_p()
+    code = lib().bf_last_cuda_error(ctypes.byref(name))
+    return code, (name.value or b"").decode()

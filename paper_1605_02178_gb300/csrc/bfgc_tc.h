@@ -1,6 +1,8 @@
 // Geometry and launchers of the fused tensor-core form (k_rows_tc.cu: row pass with the
 // Toeplitz operand in tensor memory, the default; k_umma.cu: row pass with the Toeplitz
-// operand in shared memory and a chosen tile width; k_tc.cu: column pass + ratio).
+// operand in shared memory and a chosen tile width; k_cols_tc.cu: column pass + ratio with two
+// channels per MMA step, for ceil(R/16) <= 7; k_tc.cu: column pass + ratio with one channel
+// per step, for ceil(R/16) = 8, and the geometry).
 #pragma once
 
 #include <cuda.h>
@@ -27,6 +29,8 @@ struct TcGeom {
     int r_rows;       // padded rows per tile: floor(128 / C) (fewer if the octets do not fit)
     int r_stages;     // channel-buffer ring depth (2 .. 4)
     int r_stg;        // staging tiles of the drain's TMA stores (1 or 2)
+    // column pass with channel pairs (k_cols_tc.cu); 0 when a > 7 (one channel per step, k_tc.cu)
+    int vp_stages;    // ring depth, stages of two channel tiles (2 .. 4)
 };
 
 // tw: row-pass tile width (64, 128 or 256; 128 and 256 only for a <= 4), 0 for the default
@@ -46,6 +50,10 @@ cudaError_t launch_build_hpass_tc(const float* f, void* Y, const GcParams& p, co
                                   bool fp16, DiagHeader* diag, cudaStream_t s);
 cudaError_t launch_build_hpass_umma(const float* f, void* Y, const GcParams& p, const Taps& t, const TcGeom& g,
                                     bool fp16, DiagHeader* diag, cudaStream_t s);
+int vp_stages_for(int a);
+size_t vp_smem_bytes(const TcGeom& g);
+cudaError_t launch_vpass_combine_pairs(const float* f, void* Y, float* out, const GcParams& p, const Taps& t,
+                                       const TcGeom& g, bool fp16, DiagHeader* diag, cudaStream_t s);
 cudaError_t launch_vpass_combine_tc(const float* f, void* Y, float* out, const GcParams& p, const Taps& t,
                                     const TcGeom& g, bool fp16, DiagHeader* diag, cudaStream_t s);
 

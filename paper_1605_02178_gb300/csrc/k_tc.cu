@@ -1,5 +1,7 @@
 // Column pass of eq. (7) + ratio (eqs. (8)-(10)) of the fused tensor-core form, on the
-// 5th-generation tensor cores (tcgen05).  (The channel build + row pass is k_umma.cu.)
+// 5th-generation tensor cores (tcgen05), one channel per MMA step: the kernel used when
+// ceil(R/16) = 8 (k_cols_tc.cu pairs the channels for smaller radii); and the geometry of the
+// fused form.  (The channel build + row pass is k_rows_tc.cu / k_umma.cu.)
 //
 // GEMM view, per tile of 128 output rows x 64 output columns and per channel m:
 //   D[i][x] = sum_k A[i][k] Y_m[y0 + k][x0 + x],   k = 0 .. 128 + 2P - 1  (P = 16a),
@@ -440,6 +442,7 @@ TcGeom tc_geometry(int H, int W, int R, int C, int tw) {
     g.r_rows = std::max(1, std::min(128 / std::max(1, C), rows_tc_max_octets() / ((128 + 32 * g.a) / 8)));
     // ring depth and staging tiles of the tensor-memory row pass within 224 KB of shared memory
     static const int kChoices[6][2] = {{4, 2}, {3, 2}, {4, 1}, {3, 1}, {2, 2}, {2, 1}};
+    g.vp_stages = vp_stages_for(g.a);
     g.r_stages = 0;
     g.r_stg = 0;
     for (const auto& c : kChoices)
@@ -462,6 +465,7 @@ bool tc_supported(int R, int C) {
 
 cudaError_t launch_vpass_combine_tc(const float* f, void* Y, float* out, const GcParams& p, const Taps& t,
                                     const TcGeom& g, bool fp16, DiagHeader* diag, cudaStream_t s) {
+    if (g.vp_stages >= 2) return launch_vpass_combine_pairs(f, Y, out, p, t, g, fp16, diag, s);
     return fp16 ? launch_vpass_a<__half>(f, Y, out, p, t, g, diag, s)
                 : launch_vpass_a<__nv_bfloat16>(f, Y, out, p, t, g, diag, s);
 }

@@ -192,7 +192,14 @@ bool form_supported(const bf_gc_plan_s* p) {
     }
 }
 
-bf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? BF_OK : BF_ERR_CUDA; }
+// the last CUDA error a call of this thread turned into BF_ERR_CUDA (bf_last_cuda_error)
+thread_local int g_last_cuda_error = 0;
+
+bf_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return BF_OK;
+    g_last_cuda_error = (int)e;
+    return BF_ERR_CUDA;
+}
 
 // ---- optional event timing ---------------------------------------------------------
 void prof_clear(Profiler& pr) {
@@ -517,5 +524,10 @@ const char* bf_status_string(bf_status s) {
 }
 
 const char* bf_version(void) { return "bfgc 0.1 (sm_103a)"; }
+
+int bf_last_cuda_error(const char** name) {
+    if (name) *name = g_last_cuda_error ? cudaGetErrorName((cudaError_t)g_last_cuda_error) : "cudaSuccess";
+    return g_last_cuda_error;
+}
 
 }  // extern "C"

@@ -134,7 +134,10 @@ def test_uhd_sampled_outputs_match_oracle():
 # ----------------------------------------------------------------------------- fused tensor-core form
 # Stated tolerance for BF16 channel storage: 0.5 max-abs on [0, 255].  FP16 keeps 3 more
 # mantissa bits; on the convergent (sigma_r >= 40) cases it is held to 0.05.
-TC_CASES = [c for c in CONDITIONED if c[3] >= 40.0] + [(200, 300, 32.0, 50.0, 12), (150, 170, 20.0, 60.0, 8)]
+TC_CASES = [c for c in CONDITIONED if c[3] >= 40.0] + [(200, 300, 32.0, 50.0, 12), (150, 170, 20.0, 60.0, 8),
+                                                       (130, 150, 4.0, 55.0, 13),    # odd channel count
+                                                       (180, 140, 37.0, 50.0, 9),    # a = 7, odd C
+                                                       (160, 200, 42.0, 60.0, 8)]    # a = 8: one channel per step
 
 
 @pytest.mark.parametrize("prec,tol", [("bf16", 0.5), ("fp16", 0.05)])
