@@ -145,6 +145,18 @@ bf_status bf_gc_forward(bf_gc_plan_t plan, const float *d_f, float *d_out, void 
 bf_status bf_gc_forward_host(bf_gc_plan_t plan, const float *h_f, float *h_out, float *d_f,
                              float *d_out, void *d_ws, size_t ws_bytes, bf_stream_t stream);
 
+/* Streaming forward of `count` images of the plan's size held in host memory: h_out[i] =
+ * B_hat[h_f[i]] (HOST arrays of host pointers; page-locked buffers for the copies to overlap).
+ * Consecutive images overlap: while image i is filtered, image i + 1 is uploaded and image
+ * i - 1 downloaded (three internal streams ordered by events, two device slots).  d_scratch:
+ * 256-byte aligned device memory of at least bf_gc_stream_bytes bytes (two input and two
+ * output images and one forward workspace), owned by the caller.  Work queued on `stream`
+ * before the call comes first; the call returns when every output is in host memory.
+ * Per-image diagnostics are not kept. */
+bf_status bf_gc_stream_bytes(bf_gc_plan_t plan, size_t *bytes);
+bf_status bf_gc_forward_host_stream(bf_gc_plan_t plan, int count, const float *const *h_f, float *const *h_out,
+                                    void *d_scratch, size_t scratch_bytes, bf_stream_t stream);
+
 /* Adjoint of the forward (not in the paper): given d_gout = dL/dB_hat, writes
  * d_gf = dL/df (H x W) and, if d_gsigma_r is not NULL, *d_gsigma_r = dL/dsigma_r
  * (one double on the device).  The derivative is that of the approximation,

@@ -57,6 +57,8 @@ SIGNATURES = {
     "bf_gc_forward": (_I, [_P, _P, _P, _P, _SZ, _P]),
     "bf_gc_forward_host": (_I, [_P, _P, _P, _P, _P, _P, _SZ, _P]),
     "bf_gc_forward_static": (_I, [_P, _P, _P, _P]),
+    "bf_gc_stream_bytes": (_I, [_P, ctypes.POINTER(_SZ)]),
+    "bf_gc_forward_host_stream": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _P, _SZ, _P]),
     "bf_gc_backward": (_I, [_P, _P, _P, _P, _P, _P, _SZ, _P]),
     "bf_gc_diagnostics": (_I, [_P, _P, ctypes.POINTER(bf_gc_diag), _P]),
     "bf_gc_plan_destroy": (None, [_P]),
@@ -166,6 +168,24 @@ def bf_gc_forward_host(plan, h_f, h_out, d_f, d_out, ws, stream=None):
     _check(lib().bf_gc_forward_host(plan, _ptr(h_f), _ptr(h_out), _ptr(d_f), _ptr(d_out), _ptr(ws),
                                     ws.numel() * ws.element_size(), _stream(stream)), "bf_gc_forward_host")
     return h_out
+
+
+def bf_gc_stream_bytes(plan):
+    n = ctypes.c_size_t()
+    _check(lib().bf_gc_stream_bytes(plan, ctypes.byref(n)), "bf_gc_stream_bytes")
+    return n.value
+
+
+def bf_gc_forward_host_stream(plan, h_fs, h_outs, scratch, stream=None):
+    """Streaming forward of host images (float32 CPU tensors, preferably pinned) into h_outs."""
+    if len(h_fs) != len(h_outs) or not h_fs:
+        raise ValueError("h_fs and h_outs must be non-empty and of equal length")
+    pf = (_P * len(h_fs))(*[t.data_ptr() for t in h_fs])
+    po = (_P * len(h_outs))(*[t.data_ptr() for t in h_outs])
+    _check(lib().bf_gc_forward_host_stream(plan, len(h_fs), pf, po, _ptr(scratch),
+                                           scratch.numel() * scratch.element_size(), _stream(stream)),
+           "bf_gc_forward_host_stream")
+    return h_outs
 
 
 BF_STATIC_SCRATCH_BYTES = 64 << 20
