@@ -50,7 +50,7 @@ struct IirState {
 // shared-memory tile (coalesced loads and stores, conflict-free column walks).
 constexpr int IR_TILE = 32;
 
-__global__ void __launch_bounds__(32) k_iir_rows(const float* __restrict__ X, float* __restrict__ Y,
+__global__ void __launch_bounds__(32, 16) k_iir_rows(const float* __restrict__ X, float* __restrict__ Y,
                                                  float* __restrict__ tail, const GcParams p, const IirCoef c,
                                                  size_t cs) {
     __shared__ float tile[IR_TILE][IR_TILE + 1];

@@ -28,28 +28,17 @@
 
 #include "bfgc_common.cuh"
 #include "bfgc_tc.h"
+#include "bfgc_tcgen05.cuh"
 
 namespace bfgc {
 
+using namespace tc;
+
 namespace {
 
-constexpr unsigned kUmmaSpin = 1u << 22;
 constexpr int kUmmaThreads = 512;                 // 16 warps: 4 per TMEM lane quarter
 constexpr int kGenThreads = kUmmaThreads - 32;    // warps 1..15 generate channels
 constexpr int kOctSlots = 2;                      // 8-column octets per generator thread per tile
-
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
 
 // Byte offset of element (row, k) in a K-major 128-byte-swizzled tile of `rows` rows:
 // K-blocks of 64 elements (rows * 128 bytes each), 8-row groups of 1024 bytes, the 16-byte
@@ -58,55 +47,6 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int k, int rows) {
     const int kb = k >> 6, kk = k & 63;
     return (uint32_t)(kb * rows * 128 + (row >> 3) * 1024 + (row & 7) * 128 + ((((kk >> 3) ^ (row & 7))) << 4) +
                       (kk & 7) * 2);
-}
-
-// FP16 channels are stored times 2^14: |e u^n| <= 1, so the scaled channels and their
-// Gaussian averages stay below 2^14 (FP16 max 65504), while the high powers of mid-range
-// pixels move out of the FP16 subnormal range.  A power of two is exact, and a common
-// factor of every channel cancels in P/Q and in the relative division guard.
-template <typename T> struct kChannelScale { static constexpr float value = 1.0f; };
-template <> struct kChannelScale<__half> { static constexpr float value = 16384.0f; };
-
-template <typename T> __device__ __forceinline__ uint32_t pack2(float lo, float hi);
-template <> __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float lo, float hi) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&v);
-}
-template <> __device__ __forceinline__ uint32_t pack2<__half>(float lo, float hi) {
-    __half2 v = __floats2half2_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&v);
-}
-template <typename T> __device__ __forceinline__ uint16_t one16(float v);
-template <> __device__ __forceinline__ uint16_t one16<__nv_bfloat16>(float v) {
-    __nv_bfloat16 h = __float2bfloat16_rn(v);
-    return *reinterpret_cast<uint16_t*>(&h);
-}
-template <> __device__ __forceinline__ uint16_t one16<__half>(float v) {
-    __half h = __float2half_rn(v);
-    return *reinterpret_cast<uint16_t*>(&h);
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, unsigned parity) {
-    for (unsigned i = 0; i < kUmmaSpin; ++i) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
-    // load and wait in one statement: the registers are defined only once the wait is done
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-                 "tcgen05.wait::ld.sync.aligned;\n"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-                   "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-                   "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                 : "r"(taddr) : "memory");
 }
 
 __device__ __forceinline__ void fence_before_sync_after() {
@@ -216,7 +156,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_build_hpass_umma(const floa
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 u[e] = (fv[s][e] - p.t_c) * p.inv_sr;
-                v[e] = expf(-p.half_mu * u[e] * u[e]) * kChannelScale<T>::value;
+                v[e] = expf(-p.half_mu * u[e] * u[e]) * ChannelScale<T>::value;
             }
             int mrow = r * C;
             for (int c = 0; c < C; ++c, ++mrow) {
@@ -287,7 +227,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_build_hpass_umma(const floa
         if (tid == 0 && ok && tile + G < ntiles) issue_mma(b ^ 1);     // tile + G, already generated
 
         // drain tile `tile` (accumulators b), staged through A buffer b
-        if (ok && !mbar_wait_bounded(su32(&bars[b]), (unsigned)((it >> 1) & 1))) {
+        if (ok && !mbar_wait_bounded(&bars[b], (unsigned)((it >> 1) & 1))) {
             ok = false;
             atomicOr(&diag->error_flags, 2u);
         }
