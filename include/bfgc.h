@@ -80,9 +80,9 @@ enum {
                                  exact filter on 4K test images, instead of computing it exactly) */
 };
 /* Largest window radius for which BF_FORM_AUTO keeps the plain form at FP32: on a GB300 the
- * plain form costs about 1.9 ms + 0.034 ms per unit of R per 4K image (N = 20), the recursive
- * form about 4.1 ms whatever R; they cross near R = 72 (sigma_s = 24). */
-#define BF_AUTO_PLAIN_MAX_R 72
+ * plain form costs about 1.9 ms + 0.032 ms per unit of R above 15 per 4K image (N = 20), the
+ * recursive form 2.6 - 2.9 ms whatever R; they cross near R = 38 (sigma_s = 12.7). */
+#define BF_AUTO_PLAIN_MAX_R 38
 enum { BF_PREC_FP32 = 0, BF_PREC_BF16 = 1, BF_PREC_FP16 = 2 };
 enum {
     BF_POLY_CHEBYSHEV = 0,    /* c_n of eq. (19): Gauss-Chebyshev filter (GCF)          */

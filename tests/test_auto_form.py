@@ -20,8 +20,8 @@ def _form(sigma_s, precision, N=8):
 
 
 @pytest.mark.parametrize("sigma_s,precision,want", [
-    (10.0, "fp32", B.BF_FORM_PLAIN), (24.0, "fp32", B.BF_FORM_PLAIN),          # R = 30, 72
-    (24.34, "fp32", B.BF_FORM_RECURSIVE), (64.0, "fp32", B.BF_FORM_RECURSIVE),  # R = 74, 192
+    (10.0, "fp32", B.BF_FORM_PLAIN), (12.6, "fp32", B.BF_FORM_PLAIN),          # R = 30, 38
+    (13.0, "fp32", B.BF_FORM_RECURSIVE), (64.0, "fp32", B.BF_FORM_RECURSIVE),   # R = 39, 192
     (10.0, "bf16", B.BF_FORM_FUSED_TC), (42.0, "fp16", B.BF_FORM_FUSED_TC),     # R = 30, 126
     (42.7, "bf16", B.BF_FORM_RECURSIVE), (64.0, "fp16", B.BF_FORM_RECURSIVE),   # R = 129, 192
 ])
