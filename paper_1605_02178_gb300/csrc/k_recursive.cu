@@ -18,6 +18,9 @@
 // with each state value kept as an unevaluated sum hi + lo of two floats (the increment is
 // added with an error-free two-sum), so the only rounding left per step is on the small
 // increment.
+#include <algorithm>
+#include <cmath>
+
 #include "bfgc_common.cuh"
 #include "bfgc_recursive.h"
 
@@ -46,84 +49,106 @@ struct IirState {
 };
 
 // ---------------------------------------------------------------------------------------
-// Rows: one warp filters 32 rows of one plane, 32 columns at a time through a transposed
-// shared-memory tile (coalesced loads and stores, conflict-free column walks).
+// Rows: one warp filters 32 rows of one plane over one segment of the extended line, 32
+// columns at a time through a transposed shared-memory tile (coalesced loads and stores,
+// conflict-free column walks).  A line is split into segments that run in parallel (a line's
+// recursion is sequential, and C x H lines leave too few warps to hide its latency): the
+// causal pass of a segment other than the first starts `warm` samples before the segment from
+// the steady state of the sample there, and the anti-causal pass of a segment other than the
+// last `warm` samples after it from the steady state of the causal output there.  The state
+// error this leaves decays like the recursion's impulse response; `warm` is where that response
+// has fallen below 1e-8 of its peak (from the coefficients, on the host), so the segments agree
+// with the unsegmented recursion to that level.  The causal pass reads X and writes Y (the tail
+// of trailing pad samples to `tail`); the anti-causal pass reads Y and writes X, so that no
+// segment overwrites samples another segment still reads.
 constexpr int IR_TILE = 32;
 
-__global__ void __launch_bounds__(32, 16) k_iir_rows(const float* __restrict__ X, float* __restrict__ Y,
-                                                 float* __restrict__ tail, const GcParams p, const IirCoef c,
-                                                 size_t cs) {
+__global__ void __launch_bounds__(32, 16) k_iir_rows_causal(const float* __restrict__ X, float* __restrict__ Y,
+                                                        float* __restrict__ tail, const GcParams p,
+                                                        const IirCoef c, size_t cs, int seg_len, int warm) {
     __shared__ float tile[IR_TILE][IR_TILE + 1];
     const int lane = threadIdx.x;
-    const int n = p.W, P = c.P;
+    const int n = p.W, P = c.P, ext = n + 2 * P;
     const int row0 = blockIdx.x * IR_TILE, plane = blockIdx.y;
+    const int qs = blockIdx.z * seg_len;
+    if (qs >= ext) return;
+    const int qe = min(ext, qs + seg_len);
+    const int q0 = blockIdx.z == 0 ? 0 : max(0, qs - warm);
     const int myrow = row0 + lane;
-    const bool live = myrow < p.H;
     const float* src = X + (size_t)plane * cs;
     float* dst = Y + (size_t)plane * cs;
-    const int ext = n + 2 * P;
-    const int chunks = (ext + IR_TILE - 1) / IR_TILE;
+    auto xat = [&](int row, int q) {
+        const int xi = q - P;
+        return src[(size_t)row * n + ((unsigned)xi < (unsigned)n ? xi : mirror(xi, n))];
+    };
 
     IirState st;
-    {
-        const float x0 = live ? src[(size_t)myrow * n + mirror(-P, n)] : 0.0f;
-        st.init(x0);
-    }
-    // causal: chunk k covers extended positions q = 32k .. 32k+31 (x index q - P)
-    for (int k = 0; k < chunks; ++k) {
+    st.init(myrow < p.H ? xat(myrow, q0) : 0.0f);
+    for (int qc = q0; qc < qe; qc += IR_TILE) {     // chunk: positions qc .. qc + 31
         float v[IR_TILE];                             // all 32 loads in flight before any store
 #pragma unroll
-        for (int r = 0; r < IR_TILE; ++r) {          // load: row r, lane = column
-            const int row = row0 + r;
-            const int q = k * IR_TILE + lane, xi = q - P;
-            v[r] = 0.0f;
-            if (row < p.H && q < ext) v[r] = src[(size_t)row * n + ((unsigned)xi < (unsigned)n ? xi : mirror(xi, n))];
+        for (int r = 0; r < IR_TILE; ++r) {          // load: row r, lane = position
+            const int row = row0 + r, q = qc + lane;
+            v[r] = row < p.H && q < qe ? xat(row, q) : 0.0f;
         }
 #pragma unroll
         for (int r = 0; r < IR_TILE; ++r) tile[r][lane] = v[r];
         __syncwarp();
-        for (int j = 0; j < IR_TILE; ++j) {           // walk my row
-            const int q = k * IR_TILE + j;
-            if (q < ext) tile[lane][j] = st.step(c, tile[lane][j]);
-        }
+        for (int j = 0; j < IR_TILE; ++j)            // walk my row
+            if (qc + j < qe) tile[lane][j] = st.step(c, tile[lane][j]);
         __syncwarp();
-        for (int r = 0; r < IR_TILE; ++r) {          // store causal output (image part / tail)
-            const int row = row0 + r;
-            const int q = k * IR_TILE + lane, xi = q - P;
-            if (row < p.H && q < ext) {
+        for (int r = 0; r < IR_TILE; ++r) {          // store the segment's causal outputs
+            const int row = row0 + r, q = qc + lane, xi = q - P;
+            if (row < p.H && q >= qs && q < qe) {
                 if (xi >= 0 && xi < n) dst[(size_t)row * n + xi] = tile[r][lane];
                 else if (xi >= n) tail[((size_t)plane * p.H + row) * (size_t)P + (xi - n)] = tile[r][lane];
             }
         }
         __syncwarp();
     }
-    // anti-causal: from q = ext-1 down to P, chunks walked backwards
-    {
-        const float wl = st.h1;
-        st.init(wl);
-    }
-    for (int k = chunks - 1; k >= 0; --k) {
+}
+
+__global__ void __launch_bounds__(32, 16) k_iir_rows_anti(const float* __restrict__ Y, float* __restrict__ X,
+                                                      const float* __restrict__ tail, const GcParams p,
+                                                      const IirCoef c, size_t cs, int seg_len, int warm) {
+    __shared__ float tile[IR_TILE][IR_TILE + 1];
+    const int lane = threadIdx.x;
+    const int n = p.W, P = c.P, ext = n + 2 * P;
+    const int row0 = blockIdx.x * IR_TILE, plane = blockIdx.y;
+    const int qs = blockIdx.z * seg_len;
+    if (qs >= ext) return;
+    const int qe = min(ext, qs + seg_len);
+    if (qe <= P) return;                              // the segment lies in the left pad
+    const int lo = max(qs, P);                        // outputs for lo .. qe - 1 (image part)
+    const int q1 = qe == ext ? ext - 1 : min(ext - 1, qe - 1 + warm);
+    const int myrow = row0 + lane;
+    const float* w = Y + (size_t)plane * cs;
+    float* dst = X + (size_t)plane * cs;
+    auto wat = [&](int row, int q) {                  // causal output at extended position q >= P
+        const int xi = q - P;
+        return xi < n ? w[(size_t)row * n + xi] : tail[((size_t)plane * p.H + row) * (size_t)P + (xi - n)];
+    };
+
+    IirState st;
+    st.init(myrow < p.H ? wat(myrow, q1) : 0.0f);
+    for (int qc = q1 - (IR_TILE - 1); qc + IR_TILE - 1 >= lo; qc -= IR_TILE) {   // positions qc .. qc + 31
         float v[IR_TILE];
 #pragma unroll
         for (int r = 0; r < IR_TILE; ++r) {
-            const int row = row0 + r;
-            const int q = k * IR_TILE + lane, xi = q - P;
-            v[r] = 0.0f;
-            if (row < p.H && q < ext && xi >= 0)
-                v[r] = xi < n ? dst[(size_t)row * n + xi] : tail[((size_t)plane * p.H + row) * (size_t)P + (xi - n)];
+            const int row = row0 + r, q = qc + lane;
+            v[r] = row < p.H && q >= lo && q <= q1 ? wat(row, q) : 0.0f;
         }
 #pragma unroll
         for (int r = 0; r < IR_TILE; ++r) tile[r][lane] = v[r];
         __syncwarp();
         for (int j = IR_TILE - 1; j >= 0; --j) {
-            const int q = k * IR_TILE + j;
-            if (q < ext && q >= P) tile[lane][j] = st.step(c, tile[lane][j]);
+            const int q = qc + j;
+            if (q >= lo && q <= q1) tile[lane][j] = st.step(c, tile[lane][j]);
         }
         __syncwarp();
         for (int r = 0; r < IR_TILE; ++r) {
-            const int row = row0 + r;
-            const int q = k * IR_TILE + lane, xi = q - P;
-            if (row < p.H && q < ext && xi >= 0 && xi < n) dst[(size_t)row * n + xi] = tile[r][lane];
+            const int row = row0 + r, q = qc + lane, xi = q - P;
+            if (row < p.H && q >= lo && q < qe && xi < n) dst[(size_t)row * n + xi] = tile[r][lane];
         }
         __syncwarp();
     }
@@ -180,11 +205,35 @@ __global__ void __launch_bounds__(128) k_iir_cols(const float* __restrict__ X, f
     }
 }
 
-cudaError_t launch_iir(int axis, const float* X, float* Y, float* tail, const GcParams& p, const IirCoef& c,
-                       size_t cs, int planes, cudaStream_t s) {
+// Samples after which the recursion's impulse response stays below 1e-8 of its peak (the
+// warm-up of a segment), from the coefficients, in double
+int iir_warmup(const IirCoef& c) {
+    const double a1 = c.a1, a2 = c.a2, a3 = c.a3;
+    double h1 = 1.0, h2 = 0.0, h3 = 0.0, peak = 1.0;
+    int last = 0;
+    for (int t = 1; t < 1 << 16; ++t) {
+        const double h = a1 * h1 + a2 * h2 + a3 * h3;
+        h3 = h2;
+        h2 = h1;
+        h1 = h;
+        peak = std::max(peak, std::fabs(h));
+        if (std::fabs(h) > 1e-8 * peak) last = t;
+        else if (t > 4 * last + 64) break;           // decayed for good
+    }
+    return last + 1;
+}
+
+cudaError_t launch_iir(int axis, float* X, float* Y, float* tail, const GcParams& p, const IirCoef& c, size_t cs,
+                       int planes, cudaStream_t s) {
     if (axis == 0) {
-        dim3 grid((p.H + IR_TILE - 1) / IR_TILE, planes);
-        k_iir_rows<<<grid, IR_TILE, 0, s>>>(X, Y, tail, p, c, cs);
+        // segments of at least three warm-ups (the overhead stays near a third) and at most 16
+        const int ext = p.W + 2 * c.P, warm = iir_warmup(c);
+        int seg_len = std::max({3 * warm, 256, (ext + 15) / 16});
+        seg_len = (seg_len + IR_TILE - 1) / IR_TILE * IR_TILE;
+        const int nseg = (ext + seg_len - 1) / seg_len;
+        dim3 grid((p.H + IR_TILE - 1) / IR_TILE, planes, nseg);
+        k_iir_rows_causal<<<grid, IR_TILE, 0, s>>>(X, Y, tail, p, c, cs, seg_len, warm);
+        k_iir_rows_anti<<<grid, IR_TILE, 0, s>>>(Y, X, tail, p, c, cs, seg_len, warm);
     } else {
         dim3 grid((p.W + 127) / 128, planes);
         k_iir_cols<<<grid, 128, 0, s>>>(X, Y, tail, p, c, cs);

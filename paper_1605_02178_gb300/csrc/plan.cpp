@@ -374,11 +374,11 @@ bf_status bf_gc_forward(bf_gc_plan_t p, const float* f, float* out, void* ws, si
         prof_mark(p, "build", s);
         if ((e = bfgc::launch_build(f, X, p->gp, cs, s)) != cudaSuccess) break;
         prof_mark(p, "iir_rows", s);
-        if ((e = bfgc::launch_iir(0, X, Y, tail, p->gp, ic, cs, p->C, s)) != cudaSuccess) break;
+        if ((e = bfgc::launch_iir(0, X, Y, tail, p->gp, ic, cs, p->C, s)) != cudaSuccess) break;   // result in X
         prof_mark(p, "iir_cols", s);
-        if ((e = bfgc::launch_iir(1, Y, X, tail, p->gp, ic, cs, p->C, s)) != cudaSuccess) break;
+        if ((e = bfgc::launch_iir(1, X, Y, tail, p->gp, ic, cs, p->C, s)) != cudaSuccess) break;   // result in Y
         prof_mark(p, "combine", s);
-        e = bfgc::launch_combine(f, X, out, p->gp, cs, diag, s);
+        e = bfgc::launch_combine(f, Y, out, p->gp, cs, diag, s);
         break;
     }
     default:
