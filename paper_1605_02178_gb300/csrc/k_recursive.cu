@@ -50,8 +50,9 @@ struct IirState {
 
 // ---------------------------------------------------------------------------------------
 // Rows: one warp filters 32 rows of one plane over one segment of the extended line, 32
-// columns at a time through a transposed shared-memory tile (coalesced loads and stores,
-// conflict-free column walks).  A line is split into segments that run in parallel (a line's
+// columns at a time through a transposed shared-memory tile (coalesced loads, copied straight
+// into shared memory with cp.async, coalesced stores, conflict-free column walks); four such
+// warps to a block.  A line is split into segments that run in parallel (a line's
 // recursion is sequential, and C x H lines leave too few warps to hide its latency): the
 // causal pass of a segment other than the first starts `warm` samples before the segment from
 // the steady state of the sample there, and the anti-causal pass of a segment other than the
@@ -62,37 +63,48 @@ struct IirState {
 // of trailing pad samples to `tail`); the anti-causal pass reads Y and writes X, so that no
 // segment overwrites samples another segment still reads.
 constexpr int IR_TILE = 32;
+constexpr int IR_WARPS = 4;                           // warps per block, each with its own 32 rows
 
-__global__ void __launch_bounds__(32, 16) k_iir_rows_causal(const float* __restrict__ X, float* __restrict__ Y,
-                                                        float* __restrict__ tail, const GcParams p,
-                                                        const IirCoef c, size_t cs, int seg_len, int warm) {
-    __shared__ float tile[IR_TILE][IR_TILE + 1];
-    const int lane = threadIdx.x;
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" :: "r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(IR_TILE * IR_WARPS, 8) k_iir_rows_causal(const float* __restrict__ X,
+                                                                       float* __restrict__ Y,
+                                                                       float* __restrict__ tail, const GcParams p,
+                                                                       const IirCoef c, size_t cs, int seg_len,
+                                                                       int warm) {
+    __shared__ float tiles[IR_WARPS][IR_TILE][IR_TILE + 1];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float(*tile)[IR_TILE + 1] = tiles[wid];
     const int n = p.W, P = c.P, ext = n + 2 * P;
-    const int row0 = blockIdx.x * IR_TILE, plane = blockIdx.y;
+    const int row0 = (blockIdx.x * IR_WARPS + wid) * IR_TILE, plane = blockIdx.y;
     const int qs = blockIdx.z * seg_len;
-    if (qs >= ext) return;
+    if (qs >= ext || row0 >= p.H) return;
     const int qe = min(ext, qs + seg_len);
     const int q0 = blockIdx.z == 0 ? 0 : max(0, qs - warm);
     const int myrow = row0 + lane;
     const float* src = X + (size_t)plane * cs;
     float* dst = Y + (size_t)plane * cs;
-    auto xat = [&](int row, int q) {
+    auto xptr = [&](int row, int q) {
         const int xi = q - P;
-        return src[(size_t)row * n + ((unsigned)xi < (unsigned)n ? xi : mirror(xi, n))];
+        return src + (size_t)row * n + ((unsigned)xi < (unsigned)n ? xi : mirror(xi, n));
     };
 
     IirState st;
-    st.init(myrow < p.H ? xat(myrow, q0) : 0.0f);
+    st.init(myrow < p.H ? *xptr(myrow, q0) : 0.0f);
     for (int qc = q0; qc < qe; qc += IR_TILE) {     // chunk: positions qc .. qc + 31
-        float v[IR_TILE];                             // all 32 loads in flight before any store
-#pragma unroll
-        for (int r = 0; r < IR_TILE; ++r) {          // load: row r, lane = position
+        // load: row r, lane = position, straight into shared memory
+        for (int r = 0; r < IR_TILE; ++r) {
             const int row = row0 + r, q = qc + lane;
-            v[r] = row < p.H && q < qe ? xat(row, q) : 0.0f;
+            if (row < p.H && q < qe) cp_async4(&tile[r][lane], xptr(row, q));
+            else tile[r][lane] = 0.0f;
         }
-#pragma unroll
-        for (int r = 0; r < IR_TILE; ++r) tile[r][lane] = v[r];
+        cp_async_wait_all();
         __syncwarp();
         for (int j = 0; j < IR_TILE; ++j)            // walk my row
             if (qc + j < qe) tile[lane][j] = st.step(c, tile[lane][j]);
@@ -108,15 +120,18 @@ __global__ void __launch_bounds__(32, 16) k_iir_rows_causal(const float* __restr
     }
 }
 
-__global__ void __launch_bounds__(32, 16) k_iir_rows_anti(const float* __restrict__ Y, float* __restrict__ X,
-                                                      const float* __restrict__ tail, const GcParams p,
-                                                      const IirCoef c, size_t cs, int seg_len, int warm) {
-    __shared__ float tile[IR_TILE][IR_TILE + 1];
-    const int lane = threadIdx.x;
+__global__ void __launch_bounds__(IR_TILE * IR_WARPS, 8) k_iir_rows_anti(const float* __restrict__ Y,
+                                                                     float* __restrict__ X,
+                                                                     const float* __restrict__ tail,
+                                                                     const GcParams p, const IirCoef c, size_t cs,
+                                                                     int seg_len, int warm) {
+    __shared__ float tiles[IR_WARPS][IR_TILE][IR_TILE + 1];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float(*tile)[IR_TILE + 1] = tiles[wid];
     const int n = p.W, P = c.P, ext = n + 2 * P;
-    const int row0 = blockIdx.x * IR_TILE, plane = blockIdx.y;
+    const int row0 = (blockIdx.x * IR_WARPS + wid) * IR_TILE, plane = blockIdx.y;
     const int qs = blockIdx.z * seg_len;
-    if (qs >= ext) return;
+    if (qs >= ext || row0 >= p.H) return;
     const int qe = min(ext, qs + seg_len);
     if (qe <= P) return;                              // the segment lies in the left pad
     const int lo = max(qs, P);                        // outputs for lo .. qe - 1 (image part)
@@ -124,22 +139,20 @@ __global__ void __launch_bounds__(32, 16) k_iir_rows_anti(const float* __restric
     const int myrow = row0 + lane;
     const float* w = Y + (size_t)plane * cs;
     float* dst = X + (size_t)plane * cs;
-    auto wat = [&](int row, int q) {                  // causal output at extended position q >= P
+    auto wptr = [&](int row, int q) {                 // causal output at extended position q >= P
         const int xi = q - P;
-        return xi < n ? w[(size_t)row * n + xi] : tail[((size_t)plane * p.H + row) * (size_t)P + (xi - n)];
+        return xi < n ? w + (size_t)row * n + xi : tail + ((size_t)plane * p.H + row) * (size_t)P + (xi - n);
     };
 
     IirState st;
-    st.init(myrow < p.H ? wat(myrow, q1) : 0.0f);
+    st.init(myrow < p.H ? *wptr(myrow, q1) : 0.0f);
     for (int qc = q1 - (IR_TILE - 1); qc + IR_TILE - 1 >= lo; qc -= IR_TILE) {   // positions qc .. qc + 31
-        float v[IR_TILE];
-#pragma unroll
         for (int r = 0; r < IR_TILE; ++r) {
             const int row = row0 + r, q = qc + lane;
-            v[r] = row < p.H && q >= lo && q <= q1 ? wat(row, q) : 0.0f;
+            if (row < p.H && q >= lo && q <= q1) cp_async4(&tile[r][lane], wptr(row, q));
+            else tile[r][lane] = 0.0f;
         }
-#pragma unroll
-        for (int r = 0; r < IR_TILE; ++r) tile[r][lane] = v[r];
+        cp_async_wait_all();
         __syncwarp();
         for (int j = IR_TILE - 1; j >= 0; --j) {
             const int q = qc + j;
@@ -231,9 +244,9 @@ cudaError_t launch_iir(int axis, float* X, float* Y, float* tail, const GcParams
         int seg_len = std::max({3 * warm, 256, (ext + 15) / 16});
         seg_len = (seg_len + IR_TILE - 1) / IR_TILE * IR_TILE;
         const int nseg = (ext + seg_len - 1) / seg_len;
-        dim3 grid((p.H + IR_TILE - 1) / IR_TILE, planes, nseg);
-        k_iir_rows_causal<<<grid, IR_TILE, 0, s>>>(X, Y, tail, p, c, cs, seg_len, warm);
-        k_iir_rows_anti<<<grid, IR_TILE, 0, s>>>(Y, X, tail, p, c, cs, seg_len, warm);
+        dim3 grid(((p.H + IR_TILE - 1) / IR_TILE + IR_WARPS - 1) / IR_WARPS, planes, nseg);
+        k_iir_rows_causal<<<grid, IR_TILE * IR_WARPS, 0, s>>>(X, Y, tail, p, c, cs, seg_len, warm);
+        k_iir_rows_anti<<<grid, IR_TILE * IR_WARPS, 0, s>>>(Y, X, tail, p, c, cs, seg_len, warm);
     } else {
         dim3 grid((p.W + 127) / 128, planes);
         k_iir_cols<<<grid, 128, 0, s>>>(X, Y, tail, p, c, cs);
