@@ -14,7 +14,9 @@
  *  - Images are single-channel float32, row-major, H rows by W columns, contiguous
  *    (element (y, x) at y*W + x).  Device pointers must be 16-byte aligned.
  *  - Pointers prefixed d_ are device memory, h_ host memory.  The caller owns every
- *    buffer (inputs, outputs, workspace); the library never allocates device memory.
+ *    buffer (inputs, outputs, workspace); the library allocates no device buffers of its
+ *    own, except the fixed module-scope scratch of bf_gc_forward_static and what the CUDA
+ *    runtime keeps for the streams, events and graphs of the batch and streaming calls.
  *  - Device work is enqueued asynchronously on `stream` (a cudaStream_t; NULL is
  *    the legacy default stream).  Argument errors are returned synchronously and
  *    nothing is enqueued.  Launch failures return BF_ERR_CUDA; faults during
@@ -111,7 +113,11 @@ typedef struct {
     unsigned long long n_guarded;   /* pixels with |Q| < 1e-12 sum|terms of Q|: output = input */
     unsigned long long n_illcond;   /* pixels with |Q| < 1e-3 sum|terms of Q| (divided like the
                                        rest, in FP32; a conditioning diagnostic) */
-    unsigned int error_flags;       /* bit 0: a bounded wait timed out in a pipelined kernel */
+    unsigned int error_flags;       /* nonzero: a bounded wait in a pipelined kernel gave up and
+                                       the output is incomplete.  Bit 0: column pass (one channel
+                                       per step), bit 1: row pass with the Toeplitz operand in
+                                       shared memory, bit 2: row pass with it in tensor memory,
+                                       bit 3: column pass (channel pairs) */
 } bf_gc_diag;
 
 /* Create a plan for H x W images (Sec. III-B): fits, in FP64 on the host, the
