@@ -11,6 +11,9 @@ namespace bfgc {
 namespace tc {
 
 constexpr unsigned kWaitNs = 1000000000u;        // bound of one mbarrier wait (1 s)
+// Taps staged in shared memory for the Toeplitz fills: the lanes of a warp read different taps,
+// and reading them from the kernel-parameter bank serialises (one access per distinct address)
+constexpr int kTapsSmem = 132;                   // >= R + 1 for R <= 128 (ceil(R/16) <= 8)
 constexpr unsigned kSuspendNs = 20000u;          // suspend-time hint of one try_wait
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }

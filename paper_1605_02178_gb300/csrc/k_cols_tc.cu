@@ -101,6 +101,8 @@ __global__ void __launch_bounds__(kPThreads, 1) k_vpass_combine_pairs(
     const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;
     const int total = my_tiles * CP;                    // pair steps of this CTA
 
+    __shared__ float s_g[kTapsSmem];
+    for (int j = tid; j <= t.R; j += blockDim.x) s_g[j] = t.g[j];
     // ---- set-up: TMEM, barriers
     if (warp == kPEpiWarps) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" :: "r"(su32(tslot)), "r"(512));
@@ -131,7 +133,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_vpass_combine_pairs(
         const int i = 32 * warp + lane;
         auto tap = [&](int k) {
             const int d = k - P - i, ad = d < 0 ? -d : d;
-            return ad <= t.R ? t.g[ad] : 0.0f;
+            return ad <= t.R ? s_g[ad] : 0.0f;
         };
         for (int c0 = 0; c0 < ACOLS; c0 += 8) {
             uint32_t r[8];

@@ -94,7 +94,7 @@ __device__ __forceinline__ void drain_sync() { asm volatile("bar.sync 1, %0;\n" 
 
 // Shared layout (1024-byte aligned): S stages of KB K-blocks | NS staging tiles | full[S] |
 // empty[S] | dfull[2] | dempty[2] | TMEM slot | abort flag | last tile committed per
-// accumulator buffer [2] | drain go flag.
+// accumulator buffer [2] | drain go flag | taps [kTapsSmem].
 template <typename T, int A_>
 __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_constant__ CUtensorMap ymap,
                                                                  const float* __restrict__ f, const GcParams p,
@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     volatile int* last_d = abort_flag + 1;
     volatile int* go = last_d + 2;
+    float* s_g = reinterpret_cast<float*>(smem + (size_t)S * SB + (size_t)NS * kRStgBytes + (2 * S + 4) * 8 + 32);
     const int tiles_x = (g.Wp + kRTile - 1) / kRTile, tiles_y = (g.Hp + TR - 1) / TR;
     const int ntiles = tiles_x * tiles_y, G = gridDim.x;
     const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;
@@ -138,6 +139,7 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
+    for (int j = tid; j <= t.R; j += blockDim.x) s_g[j] = t.g[j];
     for (int idx = tid; idx < S * (kRN - M) * KB * 8; idx += blockDim.x) {      // 16-byte chunks
         const int s = idx / ((kRN - M) * KB * 8), rem = idx % ((kRN - M) * KB * 8);
         const int row = M + rem / (KB * 8), ch = rem % (KB * 8);
@@ -157,7 +159,7 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
         const int i = 32 * warp + lane;
         auto tap = [&](int k) {
             const int d = k - 16 * a - i, ad = d < 0 ? -d : d;
-            return ad <= t.R ? t.g[ad] : 0.0f;
+            return ad <= t.R ? s_g[ad] : 0.0f;
         };
         for (int c0 = 0; c0 < ACOLS; c0 += 8) {
             uint32_t r[8];
@@ -400,7 +402,7 @@ size_t rows_tc_stg_bytes() { return kRStgBytes; }
 
 size_t rows_tc_smem_bytes(const TcGeom& g) {
     return (size_t)g.r_stages * rows_tc_stage_bytes(g.a) + (size_t)g.r_stg * kRStgBytes + (2 * g.r_stages + 4) * 8 +
-           32 + 1024;
+           32 + kTapsSmem * 4 + 1024;
 }
 
 template <typename T, int A_>

@@ -119,6 +119,8 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
     auto stage_of = [&](int j) { return (j & 1) * S2 + (j >> 1) % S2; };
     auto buf_of = [&](int j) { return (j & 1) * NB2 + (j >> 1) % NB2; };
 
+    __shared__ float s_g[kTapsSmem];
+    for (int j = tid; j <= t.R; j += blockDim.x) s_g[j] = t.g[j];
     // ---- set-up: TMEM, barriers
     if (warp == kEpiWarps) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" :: "r"(su32(tslot)), "r"(512));
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
         const int i = 32 * warp + lane;
         auto tap = [&](int k) {
             const int d = k - P - i, ad = d < 0 ? -d : d;
-            return ad <= t.R ? t.g[ad] : 0.0f;
+            return ad <= t.R ? s_g[ad] : 0.0f;
         };
         for (int c0 = 0; c0 < ACOLS; c0 += 8) {
             uint32_t r[8];

@@ -99,11 +99,14 @@ __global__ void __launch_bounds__(kUmmaThreads, 1) k_build_hpass_umma(const floa
         const int row = M + rem / (64 * g.u_nkb), k = rem % (64 * g.u_nkb);
         *reinterpret_cast<uint16_t*>(As[b] + sw128_off(row, k, 128)) = 0;
     }
+    __shared__ float s_g[kTapsSmem];
+    for (int j = tid; j <= t.R; j += blockDim.x) s_g[j] = t.g[j];
+    __syncthreads();
     for (int idx = tid; idx < 64 * 64 * g.u_kbb; idx += blockDim.x) {
         const int n = idx / (64 * g.u_kbb), k = idx % (64 * g.u_kbb);
         const int d = k - 16 * a - n;
         const int ad = d < 0 ? -d : d;
-        *reinterpret_cast<uint16_t*>(Bs + sw128_off(n, k, 64)) = one16<T>(ad <= t.R ? t.g[ad] : 0.0f);
+        *reinterpret_cast<uint16_t*>(Bs + sw128_off(n, k, 64)) = one16<T>(ad <= t.R ? s_g[ad] : 0.0f);
     }
 
     // ---- channel generation: every column the MMAs read (the band's k-steps reach 16a
