@@ -128,7 +128,9 @@ __global__ void __launch_bounds__(kPThreads, 1) k_vpass_combine_pairs(
     const uint32_t tbase = *tslot;
     const uint32_t tacc = tbase + (uint32_t)(512 - NB * 128);        // accumulator buffers
 
-    // ---- the Toeplitz operand into tensor memory: warp q < 4 writes lanes 32q .. 32q + 31
+    // ---- the Toeplitz operand into tensor memory: warp q < 4 writes lanes 32q .. 32q + 31.  Only
+    // the MMA issuer reads it, so only the writers and the issuer meet on a named barrier (2);
+    // the TMA producer and the epilogue's input staging start at once.
     if (warp < 4) {
         const int i = 32 * warp + lane;
         auto tap = [&](int k) {
@@ -142,10 +144,9 @@ __global__ void __launch_bounds__(kPThreads, 1) k_vpass_combine_pairs(
             tmem_st8(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, r);
         }
         asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        asm volatile("bar.sync 2, 160;\n" ::: "memory");
     }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 
     if (warp == kPEpiWarps) {
         // ------------------------------------------------------------ TMA producer
@@ -170,6 +171,8 @@ __global__ void __launch_bounds__(kPThreads, 1) k_vpass_combine_pairs(
         }
     } else if (warp == kPEpiWarps + 1) {
         // ------------------------------------------------------------ MMA issuer
+        asm volatile("bar.sync 2, 160;\n" ::: "memory");          // the Toeplitz operand is written
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         if (lane == 0) {
             // D f32 (bit 4); A, B f16 (0) or bf16 (1) at bits 7, 10; A K-major (bit 15 = 0),
             // B MN-major (bit 16 = 1); N / 8 at bit 17, M / 16 at bit 24

@@ -121,6 +121,49 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
     const int ntiles = tiles_x * tiles_y, G = gridDim.x;
     const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;
 
+    // ---- build warps: the f values of their first tile are fetched before the set-up, so that
+    // the loads run while tensor memory, barriers and the Toeplitz operand are prepared
+    const bool is_build = warp >= kRDrainWarps && warp < kRDrainWarps + kRGenWarps;
+    const int NG = min(kRGroups, S);               // active build groups
+    const int grp = (warp - kRDrainWarps) / kRGroupWarps;              // builds tiles grp, grp + NG, ...
+    const int gtid = tid - 32 * (kRDrainWarps + kRGroupWarps * grp);   // 0 .. kRGroupThreads - 1
+    const int noct = TR * NO;                      // <= kRGroupThreads * kROctSlots (host checks)
+    const bool vec = (p.W & 3) == 0;               // 16-byte aligned rows of f
+    float fv[kROctSlots][8];
+    auto load_f = [&](int tile) {
+        const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+        const int p0 = ty * TR, xs0 = tx * kRTile - 16 * a;
+#pragma unroll
+        for (int s = 0; s < kROctSlots; ++s) {
+            const int o = gtid + s * kRGroupThreads;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) fv[s][e] = 0.0f;
+            if (tile < ntiles && o < noct) {
+                const int r = o / NO, j = o - r * NO;
+                const int pr = p0 + r;
+                if (pr < g.Hp) {
+                    int y = pr - g.P;
+                    y = (unsigned)y < (unsigned)p.H ? y : mirror(y, p.H);
+                    const float* frow = f + (size_t)y * p.W;
+                    const int xs = xs0 + 8 * j;
+                    if (vec && xs >= 0 && xs + 8 <= p.W) {
+                        const float4 a0 = __ldg(reinterpret_cast<const float4*>(frow + xs));
+                        const float4 a1 = __ldg(reinterpret_cast<const float4*>(frow + xs + 4));
+                        fv[s][0] = a0.x; fv[s][1] = a0.y; fv[s][2] = a0.z; fv[s][3] = a0.w;
+                        fv[s][4] = a1.x; fv[s][5] = a1.y; fv[s][6] = a1.z; fv[s][7] = a1.w;
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int x = xs + e;
+                            fv[s][e] = __ldg(frow + ((unsigned)x < (unsigned)p.W ? x : mirror(x, p.W)));
+                        }
+                    }
+                }
+            }
+        }
+    };
+    if (is_build && grp < NG) load_f((int)blockIdx.x + grp * G);
+
     // ---- set-up: TMEM, barriers, row table, zero product rows M .. 127 of every stage
     if (warp == kRDrainWarps + kRGenWarps) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" :: "r"(su32(tslot)), "r"(512));
@@ -173,46 +216,8 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 
-    if (warp >= kRDrainWarps && warp < kRDrainWarps + kRGenWarps) {
+    if (is_build) {
         // ------------------------------------------------------------ channel build
-        const int NG = min(kRGroups, S);               // active build groups
-        const int grp = (warp - kRDrainWarps) / kRGroupWarps;              // builds tiles grp, grp + NG, ...
-        const int gtid = tid - 32 * (kRDrainWarps + kRGroupWarps * grp);   // 0 .. kRGroupThreads - 1
-        const int noct = TR * NO;                      // <= kRGroupThreads * kROctSlots (host checks)
-        const bool vec = (p.W & 3) == 0;               // 16-byte aligned rows of f
-        float fv[kROctSlots][8];
-        auto load_f = [&](int tile) {
-            const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
-            const int p0 = ty * TR, xs0 = tx * kRTile - 16 * a;
-#pragma unroll
-            for (int s = 0; s < kROctSlots; ++s) {
-                const int o = gtid + s * kRGroupThreads;
-#pragma unroll
-                for (int e = 0; e < 8; ++e) fv[s][e] = 0.0f;
-                if (tile < ntiles && o < noct) {
-                    const int r = o / NO, j = o - r * NO;
-                    const int pr = p0 + r;
-                    if (pr < g.Hp) {
-                        int y = pr - g.P;
-                        y = (unsigned)y < (unsigned)p.H ? y : mirror(y, p.H);
-                        const float* frow = f + (size_t)y * p.W;
-                        const int xs = xs0 + 8 * j;
-                        if (vec && xs >= 0 && xs + 8 <= p.W) {
-                            const float4 a0 = __ldg(reinterpret_cast<const float4*>(frow + xs));
-                            const float4 a1 = __ldg(reinterpret_cast<const float4*>(frow + xs + 4));
-                            fv[s][0] = a0.x; fv[s][1] = a0.y; fv[s][2] = a0.z; fv[s][3] = a0.w;
-                            fv[s][4] = a1.x; fv[s][5] = a1.y; fv[s][6] = a1.z; fv[s][7] = a1.w;
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) {
-                                const int x = xs + e;
-                                fv[s][e] = __ldg(frow + ((unsigned)x < (unsigned)p.W ? x : mirror(x, p.W)));
-                            }
-                        }
-                    }
-                }
-            }
-        };
         // build tile `it` from `fv`, hand it to the MMA issuer, then fetch the group's next tile
         auto build = [&](int it) -> bool {
             const int s = it % S, use = it / S;
@@ -267,11 +272,9 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
         // stage it % S is refilled for tile it after the MMAs of tile it - S; the group's previous
         // wait (tile it - NG) covered tile it - NG - S >= it - 2S, so the phase before the awaited
         // one is complete (NG <= S)
-        if (grp < NG) {
-            load_f((int)blockIdx.x + grp * G);
+        if (grp < NG)
             for (int it = grp; it < my_tiles; it += NG)
                 if (!build(it)) break;
-        }
     } else if (warp == kRDrainWarps + kRGenWarps) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
