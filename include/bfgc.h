@@ -79,12 +79,16 @@ enum {
                                  recursive form; with FP32 the plain form while R <= BF_AUTO_PLAIN_MAX_R,
                                  else the recursive form (whose cost does not grow with sigma_s;
                                  it approximates the Gaussian of eq. (7), 57-65 dB PSNR against the
-                                 exact filter on 4K test images, instead of computing it exactly) */
+                                 exact filter on 4K test images, instead of computing it exactly,
+                                 so AUTO takes it only where the exact forms cost at least twice
+                                 as much or do not exist) */
 };
-/* Largest window radius for which BF_FORM_AUTO keeps the plain form at FP32: on a GB300 the
- * plain form costs about 1.9 ms + 0.032 ms per unit of R above 15 per 4K image (N = 20), the
- * recursive form 2.6 - 2.9 ms whatever R; they cross near R = 38 (sigma_s = 12.7). */
-#define BF_AUTO_PLAIN_MAX_R 38
+/* Largest window radius for which BF_FORM_AUTO keeps the plain form at FP32.  AUTO keeps an
+ * exact form of eq. (7) while it costs at most twice the recursive form, which is faster but
+ * a different, less accurate filter (57-65 dB against the exact one): on a GB300 at 4K, N = 20,
+ * the plain form costs 1.9 ms at R = 15, 4.0 ms at R = 72 and 5.6 ms at R = 96, the recursive
+ * form 2.3 - 2.8 ms whatever R; twice the recursive cost is reached near R = 86 (sigma_s = 29). */
+#define BF_AUTO_PLAIN_MAX_R 86
 enum { BF_PREC_FP32 = 0, BF_PREC_BF16 = 1, BF_PREC_FP16 = 2 };
 enum {
     BF_POLY_CHEBYSHEV = 0,    /* c_n of eq. (19): Gauss-Chebyshev filter (GCF)          */

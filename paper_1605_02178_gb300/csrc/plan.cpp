@@ -172,7 +172,8 @@ size_t bwd_workspace(const bf_gc_plan_s* p) {
 }
 
 // BF_FORM_AUTO: the tensor-core form with 16-bit storage while it exists (R <= 128), the plain
-// form at FP32 up to the measured crossover, the recursive form beyond either
+// form at FP32 while it costs at most twice the recursive form (measured), the recursive form
+// beyond either
 int auto_form(const bf_gc_plan_s* p) {
     if (p->precision != BF_PREC_FP32) return bfgc::tc_supported(p->R, p->C) ? BF_FORM_FUSED_TC : BF_FORM_RECURSIVE;
     return p->R <= BF_AUTO_PLAIN_MAX_R ? BF_FORM_PLAIN : BF_FORM_RECURSIVE;

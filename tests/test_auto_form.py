@@ -20,8 +20,8 @@ def _form(sigma_s, precision, N=8):
 
 
 @pytest.mark.parametrize("sigma_s,precision,want", [
-    (10.0, "fp32", B.BF_FORM_PLAIN), (12.6, "fp32", B.BF_FORM_PLAIN),          # R = 30, 38
-    (13.0, "fp32", B.BF_FORM_RECURSIVE), (64.0, "fp32", B.BF_FORM_RECURSIVE),   # R = 39, 192
+    (10.0, "fp32", B.BF_FORM_PLAIN), (28.6, "fp32", B.BF_FORM_PLAIN),          # R = 30, 86
+    (28.7, "fp32", B.BF_FORM_RECURSIVE), (64.0, "fp32", B.BF_FORM_RECURSIVE),   # R = 87, 192
     (10.0, "bf16", B.BF_FORM_FUSED_TC), (42.0, "fp16", B.BF_FORM_FUSED_TC),     # R = 30, 126
     (42.7, "bf16", B.BF_FORM_RECURSIVE), (64.0, "fp16", B.BF_FORM_RECURSIVE),   # R = 129, 192
 ])
@@ -60,7 +60,7 @@ def test_auto_recursive_with_16bit_storage_has_no_backward_but_a_forward_workspa
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("sigma_s,precision,form", [(10.0, "bf16", "fused_tc"), (50.0, "bf16", "recursive"),
-                                                    (10.0, "fp32", "plain"), (30.0, "fp32", "recursive")])
+                                                    (10.0, "fp32", "plain"), (32.0, "fp32", "recursive")])
 def test_auto_plan_computes_the_chosen_form(sigma_s, precision, form):
     f = torch.from_numpy(synth.edge_smooth_image(150, 170, seed=21)).cuda()
     auto = api.GCPlan(150, 170, sigma_s, 50.0, 12, form="auto", precision=precision).forward(f)
