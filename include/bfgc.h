@@ -73,7 +73,7 @@ enum {
                                  spatial Gaussian as a banded Toeplitz product on tensor cores;
                                  channels stored as BF16 or FP16, FP32 accumulation */
     BF_FORM_RECURSIVE = 2,    /* recursive (IIR) stand-in for eq. (7), Young-van Vliet 1995 */
-    BF_FORM_AUTO = 3          /* chosen from R and the precision, and re-chosen when the precision
+    BF_FORM_AUTO = 3,         /* chosen from R and the precision, and re-chosen when the precision
                                  changes (bf_gc_plan_info reports the choice): with BF16 / FP16
                                  storage the tensor-core form while R <= 128 (its limit), else the
                                  recursive form; with FP32 the plain form while R <= BF_AUTO_PLAIN_MAX_R,
@@ -82,6 +82,11 @@ enum {
                                  exact filter on 4K test images, instead of computing it exactly,
                                  so AUTO takes it only where the exact forms cost at least twice
                                  as much or do not exist) */
+    BF_FORM_FUSED = 4         /* 2 kernels on the FP32 ALUs: (build + row filter) and (column filter
+                                 + ratio); FP32 channel planes between them (C planes instead of the
+                                 plain form's 2 C), the same results as PLAIN bit for bit.  Needs
+                                 FP32 and R <= 173 (its shared-memory windows), else
+                                 BF_ERR_UNSUPPORTED at bf_gc_forward. */
 };
 /* Largest window radius for which BF_FORM_AUTO keeps the plain form at FP32.  AUTO keeps an
  * exact form of eq. (7) while it costs at most twice the recursive form, which is faster but

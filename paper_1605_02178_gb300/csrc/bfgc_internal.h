@@ -86,6 +86,14 @@ cudaError_t launch_vpass(const float* X, float* Y, const GcParams& p, const Taps
 cudaError_t launch_combine(const float* f, const float* Z, float* out, const GcParams& p,
                            size_t cs, DiagHeader* diag, cudaStream_t s);
 
+// fused FP32 form: (build + row pass) -> C row-filtered planes of stride cs -> (column pass +
+// ratio); false / cudaErrorInvalidValue where its shared-memory windows do not fit (large R)
+bool fused_f32_supported(int R);
+cudaError_t launch_build_hpass_f32(const float* f, float* Y, const GcParams& p, const Taps& t, size_t cs,
+                                   cudaStream_t s);
+cudaError_t launch_vpass_combine_f32(const float* f, const float* Y, float* out, const GcParams& p, const Taps& t,
+                                     size_t cs, DiagHeader* diag, cudaStream_t s);
+
 // exact filter of eq. (1)
 cudaError_t launch_direct(const float* f, float* out, int H, int W, int R, double sigma_s,
                           double sigma_r, cudaStream_t s);

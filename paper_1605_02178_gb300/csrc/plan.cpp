@@ -135,6 +135,8 @@ size_t fwd_workspace(const bf_gc_plan_s* p) {
     switch (p->form) {
     case BF_FORM_PLAIN:
         return BF_WS_HEADER + 2 * (size_t)p->C * bfgc::plain_plane_stride(p->H, p->W) * sizeof(float);
+    case BF_FORM_FUSED:
+        return BF_WS_HEADER + (size_t)p->C * bfgc::plain_plane_stride(p->H, p->W) * sizeof(float);
     case BF_FORM_FUSED_TC:
         return BF_WS_HEADER + round_up(bfgc::tc_workspace_bytes(bfgc::tc_geometry(p->H, p->W, p->R, p->C, p->tile_w), p->C), 256);
     case BF_FORM_RECURSIVE:
@@ -183,6 +185,8 @@ bool form_supported(const bf_gc_plan_s* p) {
     switch (p->form) {
     case BF_FORM_PLAIN:
         return p->precision == BF_PREC_FP32;
+    case BF_FORM_FUSED:
+        return p->precision == BF_PREC_FP32 && bfgc::fused_f32_supported(p->R);
     case BF_FORM_FUSED_TC:
         return (p->precision == BF_PREC_BF16 || p->precision == BF_PREC_FP16) && bfgc::tc_supported(p->R, p->C);
     case BF_FORM_RECURSIVE:
@@ -265,7 +269,7 @@ bf_status bf_gc_plan_set(bf_gc_plan_t p, int option, double value) {
     const int iv = (int)value;
     switch (option) {
     case BF_OPT_FORM:
-        if (iv != value || iv < BF_FORM_PLAIN || iv > BF_FORM_AUTO) return BF_ERR_INVALID_ARG;
+        if (iv != value || iv < BF_FORM_PLAIN || iv > BF_FORM_FUSED) return BF_ERR_INVALID_ARG;
         p->form_auto = iv == BF_FORM_AUTO;
         p->form = p->form_auto ? auto_form(p) : iv;
         return BF_OK;
@@ -352,6 +356,15 @@ bf_status bf_gc_forward(bf_gc_plan_t p, const float* f, float* out, void* ws, si
         if ((e = bfgc::launch_vpass(Y, X, p->gp, p->taps, cs, p->C, s)) != cudaSuccess) break;
         prof_mark(p, "combine", s);
         e = bfgc::launch_combine(f, X, out, p->gp, cs, diag, s);
+        break;
+    }
+    case BF_FORM_FUSED: {
+        const size_t cs = bfgc::plain_plane_stride(p->H, p->W);
+        float* Y = (float*)body;
+        prof_mark(p, "build_hpass_f32", s);
+        if ((e = bfgc::launch_build_hpass_f32(f, Y, p->gp, p->taps, cs, s)) != cudaSuccess) break;
+        prof_mark(p, "vpass_combine_f32", s);
+        e = bfgc::launch_vpass_combine_f32(f, Y, out, p->gp, p->taps, cs, diag, s);
         break;
     }
     case BF_FORM_FUSED_TC: {

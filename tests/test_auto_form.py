@@ -46,7 +46,7 @@ def test_auto_form_follows_precision_changes_and_explicit_forms():
         with pytest.raises(B.BfError):                              # recursive is FP32-only outside AUTO
             B.bf_gc_workspace_size(p)
         with pytest.raises(B.BfError):
-            B.bf_gc_plan_set(p, B.BF_OPT_FORM, 4)
+            B.bf_gc_plan_set(p, B.BF_OPT_FORM, 5)
     finally:
         B.bf_gc_plan_destroy(p)
 
