@@ -76,8 +76,8 @@ enum {
     BF_FORM_AUTO = 3,         /* chosen from R and the precision, and re-chosen when the precision
                                  changes (bf_gc_plan_info reports the choice): with BF16 / FP16
                                  storage the tensor-core form while R <= 128 (its limit), else the
-                                 recursive form; with FP32 the plain form while R <= BF_AUTO_PLAIN_MAX_R,
-                                 else the recursive form (whose cost does not grow with sigma_s;
+                                 recursive form; with FP32 the fused form (BF_FORM_FUSED) while
+                                 R <= BF_AUTO_FP32_EXACT_MAX_R, else the recursive form (whose cost does not grow with sigma_s;
                                  it approximates the Gaussian of eq. (7), 57-65 dB PSNR against the
                                  exact filter on 4K test images, instead of computing it exactly,
                                  so AUTO takes it only where the exact forms cost at least twice
@@ -88,12 +88,13 @@ enum {
                                  FP32 and R <= 173 (its shared-memory windows), else
                                  BF_ERR_UNSUPPORTED at bf_gc_forward. */
 };
-/* Largest window radius for which BF_FORM_AUTO keeps the plain form at FP32.  AUTO keeps an
- * exact form of eq. (7) while it costs at most twice the recursive form, which is faster but
- * a different, less accurate filter (57-65 dB against the exact one): on a GB300 at 4K, N = 20,
- * the plain form costs 1.9 ms at R = 15, 4.0 ms at R = 72 and 5.6 ms at R = 96, the recursive
- * form 2.3 - 2.8 ms whatever R; twice the recursive cost is reached near R = 86 (sigma_s = 29). */
-#define BF_AUTO_PLAIN_MAX_R 86
+/* Largest window radius for which BF_FORM_AUTO keeps an exact form at FP32 (the fused form,
+ * BF_FORM_FUSED).  AUTO keeps an exact form of eq. (7) while it costs at most twice the
+ * recursive form, which is faster at large R but a different, less accurate filter (57-65 dB
+ * against the exact one): on a GB300 at 4K, N = 20, the fused form costs 0.86 ms at R = 15,
+ * 1.29 ms at R = 30, 3.34 ms at R = 87 and 4.99 ms at R = 141, the recursive form 2.3 - 2.6 ms
+ * whatever R; twice the recursive cost is reached at R = 141 (sigma_s = 47). */
+#define BF_AUTO_FP32_EXACT_MAX_R 140
 enum { BF_PREC_FP32 = 0, BF_PREC_BF16 = 1, BF_PREC_FP16 = 2 };
 enum {
     BF_POLY_CHEBYSHEV = 0,    /* c_n of eq. (19): Gauss-Chebyshev filter (GCF)          */

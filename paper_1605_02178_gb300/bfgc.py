@@ -18,7 +18,7 @@ BF_OK, BF_ERR_INVALID_ARG, BF_ERR_UNSUPPORTED, BF_ERR_NOMEM, BF_ERR_CUDA, BF_ERR
 BF_OPT_FORM, BF_OPT_PRECISION, BF_OPT_RANGE_L, BF_OPT_RANGE_U, BF_OPT_POLY, BF_OPT_SAVE_CHANNELS, \
     BF_OPT_TILE_W = range(1, 8)
 BF_FORM_PLAIN, BF_FORM_FUSED_TC, BF_FORM_RECURSIVE, BF_FORM_AUTO, BF_FORM_FUSED = range(5)
-BF_AUTO_PLAIN_MAX_R = 86
+BF_AUTO_FP32_EXACT_MAX_R = 140
 BF_PREC_FP32, BF_PREC_BF16, BF_PREC_FP16 = range(3)
 BF_POLY_CHEBYSHEV, BF_POLY_TAYLOR = range(2)
 BF_MAX_N = 62

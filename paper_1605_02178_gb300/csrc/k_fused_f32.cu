@@ -1,7 +1,7 @@
 // Fused form on the FP32 ALUs: two kernels instead of the plain form's four, FP32 throughout.
 //   build_hpass_f32   : f -> row-filtered channels e*u^n, n = 0..N+1   (eqs. (6), (17) and the
 //                       x axis of eq. (7)); the channels exist only in shared memory before
-//                       the row pass.
+//                       the row pass, which takes them two at a time (packed f32x2 FMA).
 //   vpass_combine_f32 : row-filtered channels -> P, Q and the ratio      (the y axis of eq. (7),
 //                       eqs. (8)-(10)); the filtered channels exist only in registers.
 // Each output takes the same FP32 operations in the same order as in the plain form (channel
@@ -35,20 +35,28 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 __host__ __device__ inline int taps_len8(int R) { return (2 * R + 1 + 7) / 8 * 8; }
 
 // ---------------------------------------------------------------------------------------
-// Row pass geometry: a block covers FR_ROWS rows x FR_COLS output columns; lane = row, warp =
-// 32-column slab, each thread produces its 32 outputs in one sweep of a 40-value register
-// window (10 LDS.128 + 2 broadcast LDS.128 per 256 FMA).
-constexpr int FR_ROWS = 32, FR_COLS = 192, FR_WARPS = FR_COLS / 32, FR_THREADS = FR_WARPS * 32;
-constexpr int FR_STAGE_PITCH = FR_COLS + 4;         // staging rows: LDS/STS.128 conflict-free
+// Row pass geometry: a block covers FR_ROWS rows x FR_COLS output columns and two channels at a
+// time.  The two channels are interleaved in shared memory, so one LDS.128 gives two aligned
+// (channel n, channel n+1) pairs and one packed fma.rn.f32x2 does the multiply-add of both
+// channels (each lane takes the same FP32 operation as the plain row pass).  Lane = row, warp =
+// 16-column slab, each thread produces its 16 output pairs in one sweep of a 24-pair window
+// (12 LDS.128 + 4 broadcast LDS.128 per 128 packed FMA).
+constexpr int FR_ROWS = 32, FR_COLS = 128, FR_WARPS = FR_COLS / 16, FR_THREADS = FR_WARPS * 32;
+constexpr int FR_STAGE_PITCH = 2 * FR_COLS + 4;     // staging rows of output pairs (pitch % 8 == 4)
 
 __host__ __device__ inline int fr_len(int R) { return (FR_COLS + 2 * R + 8 + 3) / 4 * 4; }
-__host__ __device__ inline int fr_pitch(int R) {
+__host__ __device__ inline int fr_pair_pitch(int R) {
+    int p = 2 * fr_len(R);
+    while (p % 8 != 4) p += 4;                      // LDS.128 across 8 lanes: 8 distinct 16-B slots
+    return p;
+}
+__host__ __device__ inline int fr_u_pitch(int R) {
     int p = fr_len(R);
-    while (p % 32 != 4) p += 4;                     // LDS.128 across 8 lanes: 8 distinct 16-B slots
+    while (p % 8 != 4) p += 4;
     return p;
 }
 size_t fr_smem(int R) {
-    return ((size_t)2 * FR_ROWS * fr_pitch(R) + (size_t)FR_ROWS * FR_STAGE_PITCH + taps_len8(R)) * sizeof(float);
+    return ((size_t)FR_ROWS * (fr_pair_pitch(R) + fr_u_pitch(R) + FR_STAGE_PITCH) + 2 * taps_len8(R)) * sizeof(float);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -68,93 +76,118 @@ constexpr size_t kMaxSmem = 227 * 1024;
 bool fused_f32_supported(int R) { return R >= 0 && R <= BF_MAX_R && fr_smem(R) <= kMaxSmem && fc_smem(R) <= kMaxSmem; }
 
 // ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t f2fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 __global__ void __launch_bounds__(FR_THREADS, 2)
 k_build_hpass_f32(const float* __restrict__ f, float* __restrict__ Y, const GcParams p, const Taps t, size_t cs) {
     extern __shared__ __align__(16) float smem[];
-    const int R = t.R, W = p.W, H = p.H;
-    const int LEN = fr_len(R), PITCH = fr_pitch(R), T = taps_len8(R);
-    float* ch = smem;                                  // [FR_ROWS][PITCH]: channel n over the window
-    float* us = ch + FR_ROWS * PITCH;                  // [FR_ROWS][PITCH]: u over the window
-    float* st = us + FR_ROWS * PITCH;                  // [FR_ROWS][FR_STAGE_PITCH]: outputs of channel n
-    float* g = st + FR_ROWS * FR_STAGE_PITCH;          // [T]: g[d] = tap(d - R), zero beyond 2R
+    const int R = t.R, W = p.W, H = p.H, C = p.C;
+    const int LEN = fr_len(R), PP = fr_pair_pitch(R), UP = fr_u_pitch(R), T = taps_len8(R);
+    float* pl = smem;                                  // [FR_ROWS][PP]: (channel n, n+1) pairs over the window
+    float* us = pl + FR_ROWS * PP;                     // [FR_ROWS][UP]: u over the window
+    float* st = us + FR_ROWS * UP;                     // [FR_ROWS][FR_STAGE_PITCH]: output pairs
+    float* g2 = st + FR_ROWS * FR_STAGE_PITCH;         // [T][2]: (tap(d - R), tap(d - R)), zero beyond 2R
     const int x0 = blockIdx.x * FR_COLS, y0 = blockIdx.y * FR_ROWS;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    for (int d = tid; d < T; d += FR_THREADS) g[d] = d <= 2 * R ? t.g[abs(d - R)] : 0.0f;
-    // u and channel 0 over the window (mirror extension along x, as the plain build + row pass)
+    for (int d = tid; d < T; d += FR_THREADS) {
+        const float v = d <= 2 * R ? t.g[abs(d - R)] : 0.0f;
+        *reinterpret_cast<float2*>(g2 + 2 * d) = make_float2(v, v);
+    }
+    // u, channel 0 and channel 1 over the window (mirror extension along x)
     for (int r = warp; r < FR_ROWS; r += FR_WARPS) {
         const int y = y0 + r;
-        float* crow = ch + r * PITCH;
-        float* urow = us + r * PITCH;
+        float* prow = pl + r * PP;
+        float* urow = us + r * UP;
         if (y < H) {
             const float* frow = f + (size_t)y * W;
             for (int k = lane; k < LEN; k += 32) {
                 const int x = x0 - R + k;
                 const float u = (frow[(unsigned)x < (unsigned)W ? x : mirror(x, W)] - p.t_c) * p.inv_sr;
+                const float e = expf(-p.half_mu * u * u);
                 urow[k] = u;
-                crow[k] = expf(-p.half_mu * u * u);
+                *reinterpret_cast<float2*>(prow + 2 * k) = make_float2(e, e * u);
             }
         } else {
             for (int k = lane; k < LEN; k += 32) {
                 urow[k] = 0.0f;
-                crow[k] = 0.0f;
+                *reinterpret_cast<float2*>(prow + 2 * k) = make_float2(0.0f, 0.0f);
             }
         }
     }
     __syncthreads();
 
-    const float* srow = ch + lane * PITCH + warp * 32;
-    const int LEN4 = LEN / 4;
-    for (int n = 0; n < p.C; ++n) {
-        float acc[32];
+    const float* wrow = pl + lane * PP + 2 * (warp * 16);
+    for (int n = 0; n < C; n += 2) {
+        uint64_t acc[16];
 #pragma unroll
-        for (int v = 0; v < 32; ++v) acc[v] = 0.0f;
+        for (int v = 0; v < 16; ++v) acc[v] = 0ull;
         for (int d0 = 0; d0 < T; d0 += 8) {
-            float w[40], gg[8];
+            uint64_t w[24], tp[8];
 #pragma unroll
-            for (int q = 0; q < 10; ++q)
-                *reinterpret_cast<float4*>(&w[4 * q]) = *reinterpret_cast<const float4*>(srow + d0 + 4 * q);
-            *reinterpret_cast<float4*>(&gg[0]) = *reinterpret_cast<const float4*>(g + d0);
-            *reinterpret_cast<float4*>(&gg[4]) = *reinterpret_cast<const float4*>(g + d0 + 4);
+            for (int q = 0; q < 12; ++q) {
+                const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(wrow + 2 * d0 + 4 * q);
+                w[2 * q] = v.x;
+                w[2 * q + 1] = v.y;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(g2 + 2 * d0 + 4 * q);
+                tp[2 * q] = v.x;
+                tp[2 * q + 1] = v.y;
+            }
 #pragma unroll
             for (int j = 0; j < 8; ++j)
 #pragma unroll
-                for (int v = 0; v < 32; ++v) acc[v] = fmaf(gg[j], w[v + j], acc[v]);
+                for (int v = 0; v < 16; ++v) acc[v] = f2fma(tp[j], w[v + j], acc[v]);
         }
-        __syncthreads();                               // every thread is done reading channel n
-        float* so = st + lane * FR_STAGE_PITCH + warp * 32;
+        __syncthreads();                               // every thread is done reading this pair
+        float* so = st + lane * FR_STAGE_PITCH + 2 * (warp * 16);
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-            *reinterpret_cast<float4*>(so + 4 * q) = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-        if (n + 1 < p.C) {                             // channel n+1 = channel n * u, in place
-            for (int i = tid; i < FR_ROWS * LEN4; i += FR_THREADS) {
-                const int r = i / LEN4, k = (i - r * LEN4) * 4;
-                float4 c = *reinterpret_cast<float4*>(ch + r * PITCH + k);
-                const float4 u = *reinterpret_cast<const float4*>(us + r * PITCH + k);
-                c.x *= u.x; c.y *= u.y; c.z *= u.z; c.w *= u.w;
-                *reinterpret_cast<float4*>(ch + r * PITCH + k) = c;
+        for (int v = 0; v < 16; v += 2)
+            *reinterpret_cast<ulonglong2*>(so + 2 * v) = make_ulonglong2(acc[v], acc[v + 1]);
+        if (n + 2 < C) {                               // (n+2, n+3) = (c_{n+1} u, c_{n+1} u u), in place
+            for (int r = warp; r < FR_ROWS; r += FR_WARPS) {
+                float* prow = pl + r * PP;
+                const float* urow = us + r * UP;
+                for (int k = 2 * lane; k < LEN; k += 64) {   // window positions k, k + 1
+                    float4 c = *reinterpret_cast<float4*>(prow + 2 * k);
+                    const float2 u = *reinterpret_cast<const float2*>(urow + k);
+                    c.x = c.y * u.x; c.y = c.x * u.x;
+                    c.z = c.w * u.y; c.w = c.z * u.y;
+                    *reinterpret_cast<float4*>(prow + 2 * k) = c;
+                }
             }
         }
         __syncthreads();
-        // staged outputs -> plane n, row-major and coalesced
-        float* dst = Y + (size_t)n * cs;
+        // staged output pairs -> planes n and n+1, row-major and coalesced
+        float* dst0 = Y + (size_t)n * cs;
+        float* dst1 = n + 1 < C ? dst0 + cs : nullptr;
         constexpr int Q4 = FR_COLS / 4;
         for (int i = tid; i < FR_ROWS * Q4; i += FR_THREADS) {
             const int r = i / Q4, c = (i - r * Q4) * 4;
             const int y = y0 + r, x = x0 + c;
             if (y >= H || x >= W) continue;
-            const float4 v = *reinterpret_cast<const float4*>(st + r * FR_STAGE_PITCH + c);
-            float* o = dst + (size_t)y * W + x;
+            const float4 lo = *reinterpret_cast<const float4*>(st + r * FR_STAGE_PITCH + 2 * c);
+            const float4 hi = *reinterpret_cast<const float4*>(st + r * FR_STAGE_PITCH + 2 * c + 4);
+            const float4 va = make_float4(lo.x, lo.z, hi.x, hi.z), vb = make_float4(lo.y, lo.w, hi.y, hi.w);
+            const size_t o = (size_t)y * W + x;
             if ((W & 3) == 0) {
-                *reinterpret_cast<float4*>(o) = v;
+                *reinterpret_cast<float4*>(dst0 + o) = va;
+                if (dst1) *reinterpret_cast<float4*>(dst1 + o) = vb;
             } else {
-                o[0] = v.x;
-                if (x + 1 < W) o[1] = v.y;
-                if (x + 2 < W) o[2] = v.z;
-                if (x + 3 < W) o[3] = v.w;
+                const float a4[4] = {va.x, va.y, va.z, va.w}, b4[4] = {vb.x, vb.y, vb.z, vb.w};
+                for (int e = 0; e < 4 && x + e < W; ++e) {
+                    dst0[o + e] = a4[e];
+                    if (dst1) dst1[o + e] = b4[e];
+                }
             }
         }
-        // the next pass over `st` starts after the first barrier of channel n+1, which every
+        // the next pass over `st` starts after the first barrier of the next pair, which every
         // thread reaches only after its copy above
     }
 }

@@ -173,12 +173,12 @@ size_t bwd_workspace(const bf_gc_plan_s* p) {
     return BF_WS_HEADER + (2 * (size_t)p->C + 1) * cs * sizeof(float) + 2 * bfgc::kAdjBlocks * sizeof(double);
 }
 
-// BF_FORM_AUTO: the tensor-core form with 16-bit storage while it exists (R <= 128), the plain
-// form at FP32 while it costs at most twice the recursive form (measured), the recursive form
-// beyond either
+// BF_FORM_AUTO: the tensor-core form with 16-bit storage while it exists (R <= 128), the fused
+// FP32 form at FP32 while it costs at most twice the recursive form (measured), the recursive
+// form beyond either
 int auto_form(const bf_gc_plan_s* p) {
     if (p->precision != BF_PREC_FP32) return bfgc::tc_supported(p->R, p->C) ? BF_FORM_FUSED_TC : BF_FORM_RECURSIVE;
-    return p->R <= BF_AUTO_PLAIN_MAX_R ? BF_FORM_PLAIN : BF_FORM_RECURSIVE;
+    return p->R <= BF_AUTO_FP32_EXACT_MAX_R && bfgc::fused_f32_supported(p->R) ? BF_FORM_FUSED : BF_FORM_RECURSIVE;
 }
 
 bool form_supported(const bf_gc_plan_s* p) {

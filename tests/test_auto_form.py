@@ -20,26 +20,26 @@ def _form(sigma_s, precision, N=8):
 
 
 @pytest.mark.parametrize("sigma_s,precision,want", [
-    (10.0, "fp32", B.BF_FORM_PLAIN), (28.6, "fp32", B.BF_FORM_PLAIN),          # R = 30, 86
-    (28.7, "fp32", B.BF_FORM_RECURSIVE), (64.0, "fp32", B.BF_FORM_RECURSIVE),   # R = 87, 192
+    (10.0, "fp32", B.BF_FORM_FUSED), (46.6, "fp32", B.BF_FORM_FUSED),          # R = 30, 140
+    (46.7, "fp32", B.BF_FORM_RECURSIVE), (64.0, "fp32", B.BF_FORM_RECURSIVE),  # R = 141, 192
     (10.0, "bf16", B.BF_FORM_FUSED_TC), (42.0, "fp16", B.BF_FORM_FUSED_TC),     # R = 30, 126
     (42.7, "bf16", B.BF_FORM_RECURSIVE), (64.0, "fp16", B.BF_FORM_RECURSIVE),   # R = 129, 192
 ])
 def test_auto_form_follows_radius_and_precision(sigma_s, precision, want):
     form, R = _form(sigma_s, precision)
     assert form == want, (sigma_s, precision, R, form)
-    assert (R <= B.BF_AUTO_PLAIN_MAX_R) == (form == B.BF_FORM_PLAIN) or precision != "fp32"
+    assert (R <= B.BF_AUTO_FP32_EXACT_MAX_R) == (form == B.BF_FORM_FUSED) or precision != "fp32"
 
 
 def test_auto_form_follows_precision_changes_and_explicit_forms():
     p = B.bf_gc_plan(64, 64, 10.0, 40.0, 8)
     try:
         B.bf_gc_plan_set(p, B.BF_OPT_FORM, B.BF_FORM_AUTO)
-        assert B.bf_gc_plan_info(p).form == B.BF_FORM_PLAIN
+        assert B.bf_gc_plan_info(p).form == B.BF_FORM_FUSED
         B.bf_gc_plan_set(p, B.BF_OPT_PRECISION, B.BF_PREC_BF16)
         assert B.bf_gc_plan_info(p).form == B.BF_FORM_FUSED_TC
         B.bf_gc_plan_set(p, B.BF_OPT_PRECISION, B.BF_PREC_FP32)
-        assert B.bf_gc_plan_info(p).form == B.BF_FORM_PLAIN
+        assert B.bf_gc_plan_info(p).form == B.BF_FORM_FUSED
         B.bf_gc_plan_set(p, B.BF_OPT_FORM, B.BF_FORM_RECURSIVE)     # an explicit form ends AUTO
         B.bf_gc_plan_set(p, B.BF_OPT_PRECISION, B.BF_PREC_BF16)
         assert B.bf_gc_plan_info(p).form == B.BF_FORM_RECURSIVE
@@ -60,11 +60,11 @@ def test_auto_recursive_with_16bit_storage_has_no_backward_but_a_forward_workspa
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("sigma_s,precision,form", [(10.0, "bf16", "fused_tc"), (50.0, "bf16", "recursive"),
-                                                    (10.0, "fp32", "plain"), (32.0, "fp32", "recursive")])
+                                                    (10.0, "fp32", "fused"), (50.0, "fp32", "recursive")])
 def test_auto_plan_computes_the_chosen_form(sigma_s, precision, form):
     f = torch.from_numpy(synth.edge_smooth_image(150, 170, seed=21)).cuda()
     auto = api.GCPlan(150, 170, sigma_s, 50.0, 12, form="auto", precision=precision).forward(f)
     ref = api.GCPlan(150, 170, sigma_s, 50.0, 12, form=form,
-                     precision=precision if form == "fused_tc" or form == "plain" else "fp32").forward(f)
+                     precision=precision if form == "fused_tc" else "fp32").forward(f)
     torch.cuda.synchronize()
     assert torch.equal(auto, ref)

@@ -65,7 +65,8 @@ def test_tile_width_does_not_change_the_result(H, W, ss, N, prec, tw):
 
 
 @pytest.mark.parametrize("branches", [1, 3, 8])
-@pytest.mark.parametrize("form,precision", [("fused_tc", "bf16"), ("fused_tc", "fp16"), ("plain", "fp32")])
+@pytest.mark.parametrize("form,precision", [("fused_tc", "bf16"), ("fused_tc", "fp16"), ("plain", "fp32"),
+                                            ("fused", "fp32")])
 def test_batch_equals_per_image_forwards(form, precision, branches):
     fs = _images(SMALL_SPECS)
     ref = _per_image(SMALL_SPECS, fs, form, precision)
