@@ -43,6 +43,7 @@ CASES = [
     (120, 160, 3.0, 8.0, 10, {}),          # small sigma_r: guarded and ill-conditioned pixels
     (90, 77, 4.0, 40.0, 9, {"poly": "taylor"}),
     (66, 130, 3.0, 20.0, 12, {"L": 10.0, "U": 200.0}),
+    (33, 70, 2.0, 120.0, 62, {}),          # N = 62: 64 channels, the most a plan takes
 ]
 
 
