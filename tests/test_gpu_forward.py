@@ -198,7 +198,9 @@ def test_fused_tc_matches_plain_on_constant_and_flips():
 @pytest.mark.parametrize("H,W,ss,sr,N", [(97, 131, 2.0, 50.0, 12), (64, 200, 5.0, 60.0, 10),
                                          (40, 33, 10.0, 50.0, 16), (1, 37, 2.0, 50.0, 12),
                                          (5, 3, 3.0, 50.0, 12), (150, 170, 20.0, 60.0, 8),
-                                         (96, 96, 0.7, 50.0, 12)])
+                                         (96, 96, 0.7, 50.0, 12),
+                                         # three segments along each axis (rows and columns)
+                                         (700, 650, 2.0, 50.0, 12), (520, 530, 4.0, 50.0, 10)])
 def test_recursive_forward_matches_oracle_twin(H, W, ss, sr, N):
     """Young-van Vliet recursive spatial filter: FP32 GPU against the FP64 oracle running
     the same recursion, padding and initialisation."""
