@@ -199,7 +199,7 @@ def test_fused_tc_matches_plain_on_constant_and_flips():
                                          (40, 33, 10.0, 50.0, 16), (1, 37, 2.0, 50.0, 12),
                                          (5, 3, 3.0, 50.0, 12), (150, 170, 20.0, 60.0, 8),
                                          (96, 96, 0.7, 50.0, 12),
-                                         # three segments along each axis (rows and columns)
+                                         # rows split into three segments each (warm-up joins)
                                          (700, 650, 2.0, 50.0, 12), (520, 530, 4.0, 50.0, 10)])
 def test_recursive_forward_matches_oracle_twin(H, W, ss, sr, N):
     """Young-van Vliet recursive spatial filter: FP32 GPU against the FP64 oracle running
