@@ -59,7 +59,9 @@ enum {
     BF_OPT_RANGE_U = 4,       /* value: U of the intensity range                   (default 255)   */
     BF_OPT_POLY = 5,          /* value: BF_POLY_*, choice of c_n                   (default CHEB)  */
     BF_OPT_SAVE_CHANNELS = 6, /* value: 1 = forward leaves the filtered channels in the workspace
-                                 for bf_gc_backward to reuse; 0 = backward recomputes them      */
+                                 for bf_gc_backward to reuse; 0 = backward recomputes them.
+                                 Plain form only: the other forms never hold the filtered
+                                 channels as FP32 planes, and their backward recomputes them. */
     BF_OPT_TILE_W = 7         /* value: row-pass kernel of the tensor-core form.  0 (default):
                                  Toeplitz operand in tensor memory, tiles of 128 output columns.
                                  64, 128 or 256: Toeplitz operand in shared memory, tiles of that
@@ -86,7 +88,8 @@ enum {
                                  + ratio); FP32 channel planes between them (C planes instead of the
                                  plain form's 2 C), the same results as PLAIN bit for bit.  Needs
                                  FP32 and R <= 173 (its shared-memory windows), else
-                                 BF_ERR_UNSUPPORTED at bf_gc_forward. */
+                                 BF_ERR_UNSUPPORTED from bf_gc_workspace_size and
+                                 bf_gc_forward. */
 };
 /* Largest window radius for which BF_FORM_AUTO keeps an exact form at FP32 (the fused form,
  * BF_FORM_FUSED).  AUTO keeps an exact form of eq. (7) while it costs at most twice the
