@@ -45,6 +45,7 @@ def _free_port():
 CASES = [  # H, W, sigma_s, sigma_r, N
     (29, 17, 2.0, 40.0, 8),     # R = 6, strips of 9-15 rows
     (10, 13, 2.0, 50.0, 6),     # strips of 3-5 rows, thinner than the halo (6, and 12 for the adjoint)
+    (2, 9, 1.0, 50.0, 4),       # fewer rows than three ranks: one strip is empty
 ]
 
 
