@@ -57,7 +57,7 @@ def exchange_rows(x_own, H, halo, group=None):
     e0, e1 = halo_range(H, y0, y1, halo)
     x_ext = x_own.new_empty((e1 - e0,) + tuple(x_own.shape[1:]))
     x_ext[y0 - e0:y1 - e0] = x_own
-    reqs = []
+    sends, recvs = [], []
     for peer in range(world):
         if peer == rank:
             continue
@@ -65,17 +65,17 @@ def exchange_rows(x_own, H, halo, group=None):
         q0, q1 = halo_range(H, p0, p1, halo)
         s0, s1 = max(q0, y0), min(q1, y1)           # my rows the peer needs
         if s0 < s1:
-            reqs.append(dist.isend(x_own[s0 - y0:s1 - y0].contiguous(), dst=_global(peer, group), group=group))
+            rows = x_own[s0 - y0:s1 - y0].contiguous()   # held until its send completes
+            sends.append((dist.isend(rows, dst=_global(peer, group), group=group), rows))
         r0, r1 = max(e0, p0), min(e1, p1)           # the peer's rows I need
         if r0 < r1:
             buf = x_own.new_empty((r1 - r0,) + tuple(x_own.shape[1:]))
-            reqs.append((dist.irecv(buf, src=_global(peer, group), group=group), buf, r0 - e0))
-    for r in reqs:
-        if isinstance(r, tuple):
-            r[0].wait()
-            x_ext[r[2]:r[2] + r[1].shape[0]] = r[1]
-        else:
-            r.wait()
+            recvs.append((dist.irecv(buf, src=_global(peer, group), group=group), buf, r0 - e0))
+    for req, buf, at in recvs:
+        req.wait()
+        x_ext[at:at + buf.shape[0]] = buf
+    for req, _ in sends:
+        req.wait()
     return x_ext
 
 
