@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--forms", default=None, help="comma list of form:precision to run")
     ap.add_argument("--size", default=None, help="HxW instead of 2160x3840 (profiling cases)")
-    ap.add_argument("--study", default=None, choices=["precision", "gpf", "batch", "sigma"],
+    ap.add_argument("--study", default=None, choices=["precision", "gpf", "batch", "sigma", "sweep"],
                     help="instead of the benchmark: the 8192x8192 precision sweep, the GPF/GCF table at 4K, "
                          "or the uneven 256-image batch")
     ap.add_argument("--batch-count", type=int, default=256, help="images of the batch study")
@@ -429,6 +429,9 @@ def run_study(args):
     if args.study == "sigma":
         run_sigma_study(args, dev)
         return
+    if args.study == "sweep":
+        run_sweep_study(args, dev)
+        return
     if args.study == "gpf":
         f = synth.workload("uhd")["f"]
         ft = torch.from_numpy(f).to(dev)
@@ -517,6 +520,63 @@ def run_sigma_study(args, dev):
                          "psnr_vs_exact_db": psnr(out.cpu().numpy().astype(np.float64), exact)}
             del plan, ws, out
         print(json.dumps(row), flush=True)
+
+
+def run_sweep_study(args, dev):
+    """The 4K sweep of sigma_s in {5, 10, 20} x sigma_r in {10, 30, 50} x N in {5, 10, 20}, plus the
+    anchor (sigma_s = 10, sigma_r = 30, N = 28): per configuration and form, ms per image (CUDA
+    events, 5 runs after 2 warm-ups), Mpixel/s, PSNR against the exact filter (bf_direct), and
+    max-abs against the FP64 oracle at 52 sampled pixels (4 corners + 48 random)."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1605_02178_gb300 import api, synth
+    f = synth.workload("uhd")["f"]
+    H, W = f.shape
+    ft = torch.from_numpy(f).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    rng = np.random.default_rng(3)
+    idx = np.concatenate([[0, W - 1, (H - 1) * W, H * W - 1], rng.integers(0, H * W, 48)])
+    configs = [(ss, sr, N) for ss in (5.0, 10.0, 20.0) for sr in (10.0, 30.0, 50.0) for N in (5, 10, 20)]
+    configs.append((10.0, 30.0, 28))
+    exact_key, exn = None, None
+    for ss, sr, N in configs:
+        if exact_key != (ss, sr):                     # the exact filter once per (sigma_s, sigma_r)
+            exact_key, exn = (ss, sr), bfgc_direct(ft, ss, sr)
+        ref = oracle.gcf_at(f, idx, ss, sr, N)
+        for form, prec in (("fused_tc", "bf16"), ("fused_tc", "fp16"), ("fused", "fp32")):
+            plan = api.GCPlan(H, W, ss, sr, N, form=form, precision=prec)
+            ws = plan.workspace("fwd", dev)
+            out = torch.empty_like(ft)
+            for _ in range(2):
+                plan.forward(ft, out, ws, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(5):
+                plan.forward(ft, out, ws, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / 5
+            o = out.cpu().numpy().astype(np.float64)
+            d = plan.diagnostics(ws, stream)
+            print(json.dumps({
+                "study": "sweep", "image": "uhd 3840x2160", "sigma_s": ss, "sigma_r": sr, "N": N,
+                "form": form, "precision": prec, "fit_err": plan.info["fit_err"], "ms": ms,
+                "mpixel_s": H * W / (ms * 1e-3) / 1e6, "psnr_vs_exact_db": oracle.psnr_db(o, exn),
+                "maxabs_vs_fp64_oracle_sampled": float(np.abs(o.reshape(-1)[idx] - ref).max()),
+                "samples": int(idx.size), "n_guarded": d["n_guarded"], "n_illcond": d["n_illcond"],
+                "error_flags": d["error_flags"]}), flush=True)
+            del plan, ws, out
+
+
+def bfgc_direct(ft, sigma_s, sigma_r):
+    """The exact filter of eq. (1) on the GPU (bf_direct), as a float64 host array."""
+    import numpy as np
+    import torch
+    from paper_1605_02178_gb300 import bfgc
+    ex = bfgc.bf_direct(ft, sigma_s, sigma_r)
+    torch.cuda.synchronize(ft.device)
+    return ex.cpu().numpy().astype(np.float64)
 
 
 def run_batch_study(args, dev):
