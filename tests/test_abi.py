@@ -120,3 +120,48 @@ def test_fit_error_reports_convergence():
 def test_direct_rejects_bad_arguments_without_launching():
     assert B.lib().bf_direct(0, 4, 1.0, 1.0, ctypes.c_void_p(256), ctypes.c_void_p(256), None) == B.BF_ERR_INVALID_ARG
     assert B.lib().bf_direct(4, 4, 1.0, 1.0, ctypes.c_void_p(258), ctypes.c_void_p(256), None) == B.BF_ERR_INVALID_ARG
+
+
+def header_constants():
+    """Every BF_* constant the header defines (enum members and integer #defines)."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", text, flags=re.S):
+        for name, value in re.findall(r"\b(BF_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
+            out[name] = int(value)
+    for name, value in re.findall(r"#define\s+(BF_[A-Z0-9_]+)\s+(-?\d+)\b", text):
+        out[name] = int(value)
+    return out
+
+
+def test_binding_constants_equal_the_header():
+    consts = header_constants()
+    for must in ("BF_FORM_PLAIN", "BF_FORM_FUSED", "BF_FORM_FUSED_TC", "BF_FORM_RECURSIVE", "BF_FORM_AUTO",
+                 "BF_OPT_FORM", "BF_OPT_TILE_W", "BF_PREC_FP16", "BF_AUTO_FP32_EXACT_MAX_R", "BF_MAX_N"):
+        assert must in consts, must
+    shared = [n for n in consts if hasattr(B, n)]
+    assert len(shared) >= 20
+    for name in shared:
+        assert getattr(B, name) == consts[name], name
+    assert set(B.FORMS.values()) == {v for n, v in consts.items() if n.startswith("BF_FORM_")}
+
+
+def test_bench_roofline_model_names_the_profiled_kernels():
+    """bench.py's per-kernel work model has an entry for every kernel the forward of each form
+    marks for the profiler (plan.cpp), so no kernel's roofline is silently dropped."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    src = open(os.path.join(ROOT, "paper_1605_02178_gb300", "csrc", "plan.cpp")).read()
+    body = src[src.index("bf_status bf_gc_forward("):src.index("bf_status bf_gc_forward_host(")]
+    forms = {"BF_FORM_PLAIN": "plain", "BF_FORM_FUSED": "fused", "BF_FORM_FUSED_TC": "fused_tc",
+             "BF_FORM_RECURSIVE": "recursive"}
+    cases = re.split(r"\n\s*case (BF_FORM_[A-Z_]+): \{", body)
+    seen = set()
+    for enum_name, block in zip(cases[1::2], cases[2::2]):
+        marks = set(re.findall(r'prof_mark\(p, "(\w+)"', block))
+        form = forms[enum_name]
+        prec = "fp32" if form != "fused_tc" else "bf16"
+        assert marks and marks == set(bench.kernel_model(form, prec, 22, 30)), form
+        seen.add(form)
+    assert seen == set(forms.values())
