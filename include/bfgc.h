@@ -43,7 +43,7 @@ typedef struct CUstream_st *bf_stream_t;     /* identical to cudaStream_t */
 typedef enum {
     BF_OK = 0,
     BF_ERR_INVALID_ARG = 1,   /* bad size, sigma, pointer, alignment, option or state */
-    BF_ERR_UNSUPPORTED = 2,   /* valid request this build does not implement (e.g. R too large for a form) */
+    BF_ERR_UNSUPPORTED = 2,   /* valid request the library does not implement (e.g. R too large for a form) */
     BF_ERR_NOMEM = 3,         /* host allocation failed */
     BF_ERR_CUDA = 4,          /* a CUDA runtime call or kernel launch failed */
     BF_ERR_TIMEOUT = 5,       /* a bounded device wait gave up (reported by bf_gc_diagnostics) */
