@@ -103,3 +103,47 @@ def test_strips_over_gloo_ranks_equal_the_whole_image(world):
         assert np.abs(gf - gf_ref).max() <= 1e-9 * max(1.0, np.abs(gf_ref).max())
         for k in range(world):                       # every rank holds the all-reduced sum
             assert abs(got[k][i][2] - gs_ref) <= 1e-9 * max(1.0, abs(gs_ref))
+
+
+def _group_worker(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    import oracle
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    members = [1, 2, 3]
+    group = dist.new_group(members)
+    res = None
+    if rank in members:
+        H, W, ss, sr, N = CASES[0]
+        f = np.random.default_rng(H * 100 + W).uniform(0, 255, (H, W))
+        k = dist.get_rank(group)
+        y0, y1 = strips.strip_rows(H, len(members), k)
+        out = strips.forward_strips(torch.from_numpy(f[y0:y1].copy()), H, ss, sr, N, group=group,
+                                    filter_fn=lambda fe: torch.from_numpy(oracle.gcf(fe.numpy(), ss, sr, N)))
+        res = (k, out.numpy())
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, res))
+
+
+def test_strips_over_a_subgroup_of_ranks():
+    """Strips over a process subgroup (global ranks 1-3 of 4): peers are addressed by their
+    global ranks, strips by their ranks in the group."""
+    sys.path.insert(0, ROOT)
+    import oracle
+    world, port = 4, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_group_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=300) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert got[0] is None
+    parts = sorted(v for v in got.values() if v is not None)
+    H, W, ss, sr, N = CASES[0]
+    f = np.random.default_rng(H * 100 + W).uniform(0, 255, (H, W))
+    out = np.concatenate([p[1] for p in parts])
+    assert np.abs(out - oracle.gcf(f, ss, sr, N)).max() <= 1e-9
