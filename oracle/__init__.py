@@ -52,7 +52,7 @@ def _lib():
         lib.oracle_gcf.argtypes = [_dp, I, I, D, D, I, I, D, D, _dp, D, I, _dp, _dp, _dp, _dp, _dp,
                                    ctypes.POINTER(ctypes.c_long)]
         lib.oracle_gcf_at.argtypes = [_dp, I, I, D, D, I, I, D, D, _dp, D, _i64p, L, _dp, _dp, _dp]
-        lib.oracle_gcf_kernel_direct.argtypes = [_dp, I, I, D, D, I, I, D, D, _dp, _dp]
+        lib.oracle_gcf_kernel_direct.argtypes = [_dp, I, I, D, D, I, I, D, D, _dp, _dp, _dp]
         lib.oracle_mirror_index.argtypes = [L, L]
         _LIB = lib
     return _LIB
@@ -206,16 +206,20 @@ def gcf_at(f, idx, sigma_s, sigma_r, N, L=0.0, U=255.0, c=None, delta=1e-12, R=N
     return out
 
 
-def gcf_kernel_direct(f, sigma_s, sigma_r, N, L=0.0, U=255.0, c=None, R=None):
+def gcf_kernel_direct(f, sigma_s, sigma_r, N, L=0.0, U=255.0, c=None, R=None, return_den=False):
+    """Eq. (4) with the coefficients of eq. (19) used as the range kernel of eq. (1).  With
+    return_den, also the denominator sum_j g_s(j) k(g(i), g(i - j)) per pixel."""
     f = _f64(f)
     H, W = f.shape
     R = window_radius(sigma_s) if R is None else R
     c = gcf_coeffs(N, sigma_r, L, U) if c is None else _f64(c)
     out = np.empty_like(f)
+    den = np.empty_like(f) if return_den else None
     _check(_lib().oracle_gcf_kernel_direct(_ptr(f), H, W, float(sigma_s), float(sigma_r), int(N),
-                                           R, float(L), float(U), _ptr(c), _ptr(out)),
+                                           R, float(L), float(U), _ptr(c), _ptr(out),
+                                           _ptr(den) if den is not None else None),
            "gcf_kernel_direct")
-    return out
+    return (out, den) if return_den else out
 
 
 # ----------------------------------------------------------------------------- Sec. IV metric

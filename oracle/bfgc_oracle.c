@@ -450,10 +450,13 @@ int oracle_gcf_at(const double *f, int H, int W, double sigma_s, double sigma_r,
  *   k(tau, t) = exp(-tau^2/2sr^2) exp(-t^2/2sr^2) sum_n c_n (tau t / sr^2)^n,
  *   out(i) = sum_j g_s(j) k(g(i), g(i-j)) g(i-j) / sum_j g_s(j) k(...) + t_c.
  * Exchanging the order of summation (Sec. II) turns this into eqs. (8)-(10)
- * exactly, so it must agree with oracle_gcf to rounding.
+ * exactly, so it must agree with oracle_gcf to rounding.  den_out (may be
+ * NULL) receives the denominator sum_j g_s(j) k(g(i), g(i-j)), which the same
+ * exchange equals exp(-g(i)^2/2sr^2) times Q of eq. (9).
  * ---------------------------------------------------------------------- */
 int oracle_gcf_kernel_direct(const double *f, int H, int W, double sigma_s, double sigma_r,
-                             int N, int R, double L, double U, const double *c, double *out)
+                             int N, int R, double L, double U, const double *c, double *out,
+                             double *den_out)
 {
     if (!f || !out || !c || H < 1 || W < 1 || N < 0 || R < 0) return 1;
     const double tc = 0.5 * (L + U);
@@ -475,6 +478,7 @@ int oracle_gcf_kernel_direct(const double *f, int H, int W, double sigma_s, doub
                     den += gs * k;
                 }
             out[y * W + x] = num / den + tc;
+            if (den_out) den_out[y * W + x] = den;
         }
     return 0;
 }
