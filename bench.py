@@ -143,15 +143,19 @@ def traffic_record(kernel):
 def kernel_model(form, precision, C, R):
     """Algorithmic work per pixel of each kernel: ('hbm', bytes) or ('alu', flops)."""
     s = {"fp32": 4, "bf16": 2, "fp16": 2}[precision]
+    # the FP64 refinement of the exact forms reads its list's length and, per listed pixel, a
+    # window of f: no work per pixel where nothing is listed
+    refine = {"refine_fp64": ("hbm", 0)}
     if form == "plain":
         return {"build": ("hbm", 4 + 4 * C), "hpass": ("alu", 2 * (2 * R + 1) * C),
-                "vpass": ("alu", 2 * (2 * R + 1) * C), "combine": ("hbm", 4 * C + 8)}
+                "vpass": ("alu", 2 * (2 * R + 1) * C), "combine": ("hbm", 4 * C + 8), **refine}
     if form == "fused":
-        return {"build_hpass_f32": ("alu", 2 * (2 * R + 1) * C), "vpass_combine_f32": ("alu", 2 * (2 * R + 1) * C)}
+        return {"build_hpass_f32": ("alu", 2 * (2 * R + 1) * C), "vpass_combine_f32": ("alu", 2 * (2 * R + 1) * C),
+                **refine}
     if form == "recursive":
         return {"build": ("hbm", 4 + 4 * C), "iir_rows": ("hbm", 16 * C), "iir_cols": ("hbm", 16 * C),
                 "combine": ("hbm", 4 * C + 8)}
-    return {"build_hpass_tc": ("hbm", 4 + s * C), "vpass_combine_tc": ("hbm", s * C + 8)}
+    return {"build_hpass_tc": ("hbm", 4 + s * C), "vpass_combine_tc": ("hbm", s * C + 8), **refine}
 
 
 # --------------------------------------------------------------------------- reference arm

@@ -98,6 +98,11 @@ enum {
  * 1.29 ms at R = 30, 3.34 ms at R = 87 and 4.99 ms at R = 141, the recursive form 2.3 - 2.6 ms
  * whatever R; twice the recursive cost is reached at R = 141 (sigma_s = 47). */
 #define BF_AUTO_FP32_EXACT_MAX_R 140
+/* Storage of the filtered channels (BF_OPT_PRECISION).  BF16 keeps 8 significant bits and
+ * exceeds the 0.5 max-abs tolerance against the FP64 oracle at the paper's operating point
+ * sigma_r = 30, N = 28 (0.67 measured on a test image; the high-degree terms of P and Q cancel
+ * there); FP16 (11 bits, channels stored times 2^14) stays within it (0.27).  Prefer FP16 for
+ * sigma_r <= 30 with N >= 20; BF16 is within 0.02 at sigma_r >= 40. */
 enum { BF_PREC_FP32 = 0, BF_PREC_BF16 = 1, BF_PREC_FP16 = 2 };
 enum {
     BF_POLY_CHEBYSHEV = 0,    /* c_n of eq. (19): Gauss-Chebyshev filter (GCF)          */
@@ -121,16 +126,30 @@ typedef struct {
     double c_tilde[BF_MAX_N + 1]; /* c~_n = mu^n c_n (the coefficients in u = (f - t_c)/s_r) */
 } bf_gc_info;
 
-/* Device-side diagnostics written by the last forward into its workspace. */
+/* Device-side diagnostics written by the last forward into its workspace.
+ *
+ * Division of eq. (10).  The paper assumes Q > 0; where the range-kernel fit has not
+ * converged Q can vanish or change sign.  Reading taken here (the FP64 oracle takes the same):
+ * with Qa = sum_n |c~_n u^n Fbar_n| (the sum of the absolute terms of Q), the output is the
+ * input pixel when |Q| < 1e-12 Qa or Qa = 0 ("guarded"), else P/Q + t_c.  FP32 cannot
+ * resolve Q at 1e-12 Qa, so the exact forms (PLAIN, FUSED, FUSED_TC) take that decision in
+ * FP64: a pixel whose sums in the form's own arithmetic give |Q| < r Qa (r = 1e-3 with FP32
+ * channels, 1/16 with BF16, 1/128 with FP16: above the storage's error in Q) or non-finite
+ * values is recomputed from the input image entirely in FP64 (eq. (7) as a window sum, the
+ * channels, P, Q and Qa) and guarded or divided in FP64 ("refined").  Where the fit converges
+ * no pixel comes near these thresholds and the refinement costs one empty launch.  The
+ * RECURSIVE form (its spatial filter is an IIR, which a per-pixel window cannot reproduce)
+ * decides on its FP32 sums: guarded when |Q| < 2^-17 Qa, the resolution of those sums. */
 typedef struct {
-    unsigned long long n_guarded;   /* pixels with |Q| < 1e-12 sum|terms of Q|: output = input */
-    unsigned long long n_illcond;   /* pixels with |Q| < 1e-3 sum|terms of Q| (divided like the
-                                       rest, in FP32; a conditioning diagnostic) */
+    unsigned long long n_guarded;   /* pixels whose output is the input pixel (rule above) */
+    unsigned long long n_illcond;   /* pixels divided with |Q| < 1e-3 Qa (in FP64 for the refined
+                                       pixels of the exact forms); a conditioning diagnostic */
     unsigned int error_flags;       /* nonzero: a bounded wait in a pipelined kernel gave up and
                                        the output is incomplete.  Bit 0: column pass (one channel
                                        per step), bit 1: row pass with the Toeplitz operand in
                                        shared memory, bit 2: row pass with it in tensor memory,
                                        bit 3: column pass (channel pairs) */
+    unsigned long long n_refined;   /* pixels recomputed in FP64 (exact forms; 0 for RECURSIVE) */
 } bf_gc_diag;
 
 /* Create a plan for H x W images (Sec. III-B): fits, in FP64 on the host, the
@@ -154,7 +173,11 @@ bf_status bf_gc_workspace_size(bf_gc_plan_t plan, size_t *fwd_bytes, size_t *bwd
 
 /* Forward filter, eqs. (6)-(10) with centring (17): d_out = B_hat[d_f] (H x W).
  * d_ws: device workspace of at least the forward size, 256-byte aligned; its
- * contents on entry are ignored.  d_f and d_out must not overlap. */
+ * contents on entry are ignored.  d_f and d_out must not overlap.  The division of
+ * eq. (10) follows the rule given with bf_gc_diag (FP64 refinement of the pixels the form's
+ * own arithmetic cannot resolve, in the exact forms; a second kernel launch).  The exact
+ * forms need H * W < 2^32 (32-bit pixel indices in the refinement list), else
+ * BF_ERR_UNSUPPORTED. */
 bf_status bf_gc_forward(bf_gc_plan_t plan, const float *d_f, float *d_out, void *d_ws,
                         size_t ws_bytes, bf_stream_t stream);
 
@@ -180,9 +203,11 @@ bf_status bf_gc_forward_host_stream(bf_gc_plan_t plan, int count, const float *c
  * d_gf = dL/df (H x W) and, if d_gsigma_r is not NULL, *d_gsigma_r = dL/dsigma_r
  * (one double on the device).  The derivative is that of the approximation,
  * including the dependence of mu and of the Chebyshev coefficients on sigma_r.
- * d_ws: workspace of at least the backward size.  If the plan has
- * BF_OPT_SAVE_CHANNELS = 1 and d_ws is the workspace of the last forward on the
- * same d_f, the filtered channels are reused; otherwise they are recomputed. */
+ * d_ws: workspace of at least the backward size.  With BF_OPT_SAVE_CHANNELS = 1 (plain
+ * form) the filtered channels are NOT recomputed but read from d_ws: the caller must pass
+ * the workspace of the last forward of this plan on the same d_f (allocated at the backward
+ * size, which covers the forward's); the library cannot check this, and any other buffer
+ * gives wrong gradients.  Without the option (or for the other forms) they are recomputed. */
 bf_status bf_gc_backward(bf_gc_plan_t plan, const float *d_f, const float *d_gout, float *d_gf,
                          double *d_gsigma_r, void *d_ws, size_t ws_bytes, bf_stream_t stream);
 

@@ -28,6 +28,7 @@ class GCPlan:
             raise
         self.H, self.W, self.sigma_s, self.sigma_r, self.N = H, W, sigma_s, sigma_r, N
         self.form, self.precision, self.poly, self.tile_w = form, precision, poly, tile_w
+        self.save_channels = bool(save_channels)
         self._ws = {}
 
     def __del__(self):
@@ -47,11 +48,18 @@ class GCPlan:
         return B.bf_gc_workspace_size(self.handle)
 
     def workspace(self, kind="fwd", device=None):
-        """A cached workspace tensor (uint8) large enough for the forward or the backward."""
+        """A cached workspace tensor (uint8) large enough for the forward or the backward.
+
+        With save_channels the forward leaves the filtered channels where the backward reads
+        them, so both kinds are one buffer, sized for the larger of the two."""
         device = torch.device("cuda") if device is None else torch.device(device)
         if device.type == "cuda" and device.index is None:
             device = torch.device("cuda", torch.cuda.current_device())
-        need = self.workspace_bytes()[0 if kind == "fwd" else 1]
+        fwd, bwd = self.workspace_bytes()
+        if self.save_channels:
+            kind, need = "shared", max(fwd, bwd)
+        else:
+            need = fwd if kind == "fwd" else bwd
         key = (kind, str(device))
         ws = self._ws.get(key)
         if ws is None or ws.numel() < need:
@@ -59,12 +67,19 @@ class GCPlan:
             self._ws[key] = ws
         return ws
 
+    def new_workspace(self, device):
+        """A fresh workspace for one forward and the backward that reuses its channels."""
+        fwd, bwd = self.workspace_bytes()
+        return torch.empty(max(fwd, bwd, 256), dtype=torch.uint8, device=device)
+
     def forward(self, f, out=None, ws=None, stream=None):
         out = torch.empty_like(f) if out is None else out
         ws = self.workspace("fwd", f.device) if ws is None else ws
         return B.bf_gc_forward(self.handle, f, out, ws, stream)
 
     def backward(self, f, gout, gf=None, want_sigma=True, ws=None, stream=None):
+        """dL/df and dL/dsigma_r.  With save_channels, `ws` must be the workspace of the last
+        forward of this plan on the same f (the default is the plan's shared workspace)."""
         gf = torch.empty_like(f) if gf is None else gf
         gs = torch.zeros((), dtype=torch.float64, device=f.device) if want_sigma else None
         ws = self.workspace("bwd", f.device) if ws is None else ws
@@ -77,20 +92,36 @@ class GCPlan:
 
 
 class GCBilateral(torch.autograd.Function):
-    """B_hat[f] with gradients for f and sigma_r from the library's adjoint kernels."""
+    """B_hat[f] with gradients for f and sigma_r from the library's adjoint kernels.
+
+    `sigma_r` must equal the plan's (the plan holds the Chebyshev fit for that value); its
+    gradient comes back in its own dtype and shape.  With a save_channels plan the forward
+    runs in a workspace of its own, kept for the backward, which reuses its filtered channels."""
 
     @staticmethod
     def forward(ctx, f, sigma_r, plan):
-        out = plan.forward(f.contiguous())
+        sr = float(sigma_r)
+        if abs(sr - plan.sigma_r) > 1e-12 * abs(plan.sigma_r):
+            raise ValueError(f"sigma_r = {sr} differs from the plan's {plan.sigma_r}; make a plan for it")
+        f = f.contiguous()
+        ws = plan.new_workspace(f.device) if plan.save_channels else None
+        out = plan.forward(f, ws=ws)
         ctx.save_for_backward(f)
-        ctx.plan = plan
+        ctx.plan, ctx.ws = plan, ws
+        ctx.sr_meta = (sigma_r.dtype, sigma_r.shape) if isinstance(sigma_r, torch.Tensor) else None
         return out
 
     @staticmethod
     def backward(ctx, gout):
         (f,) = ctx.saved_tensors
-        gf, gs = ctx.plan.backward(f.contiguous(), gout, want_sigma=ctx.needs_input_grad[1])
-        return gf, (gs.to(torch.float32) if gs is not None else None), None
+        ws = ctx.ws
+        if ws is None:
+            ws = ctx.plan.workspace("bwd", f.device)
+        gf, gs = ctx.plan.backward(f, gout, want_sigma=ctx.needs_input_grad[1], ws=ws)
+        ctx.ws = None
+        if gs is not None and ctx.sr_meta is not None:
+            gs = gs.to(ctx.sr_meta[0]).reshape(ctx.sr_meta[1])
+        return gf, gs, None
 
 
 def gc_bilateral(f, sigma_s, sigma_r, N, **opts):

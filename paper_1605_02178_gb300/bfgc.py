@@ -41,7 +41,7 @@ class bf_gc_info(ctypes.Structure):
 
 class bf_gc_diag(ctypes.Structure):
     _fields_ = [("n_guarded", ctypes.c_ulonglong), ("n_illcond", ctypes.c_ulonglong),
-                ("error_flags", ctypes.c_uint)]
+                ("error_flags", ctypes.c_uint), ("n_refined", ctypes.c_ulonglong)]
 
 
 class bf_kernel_time(ctypes.Structure):
@@ -127,10 +127,23 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
 
 
-def _dev_f32(t, name):
+def _dev_f32(t, name, numel=None):
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
         raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must hold {numel} elements (H x W of the plan), not {t.numel()}")
     return t
+
+
+def _dev_ws(ws):
+    if not (isinstance(ws, torch.Tensor) and ws.is_cuda and ws.is_contiguous()):
+        raise ValueError("the workspace must be a contiguous CUDA tensor")
+    return ws
+
+
+def _plan_px(plan):
+    i = bf_gc_plan_info(plan)
+    return i.H * i.W
 
 
 # ----------------------------------------------------------------------------- C-ABI mirrors
@@ -158,8 +171,10 @@ def bf_gc_workspace_size(plan):
 
 
 def bf_gc_forward(plan, f, out, ws, stream=None):
-    _dev_f32(f, "f")
-    _dev_f32(out, "out")
+    px = _plan_px(plan)
+    _dev_f32(f, "f", px)
+    _dev_f32(out, "out", px)
+    _dev_ws(ws)
     _check(lib().bf_gc_forward(plan, _ptr(f), _ptr(out), _ptr(ws), ws.numel() * ws.element_size(),
                                _stream(stream)), "bf_gc_forward")
     return out
@@ -194,13 +209,23 @@ BF_STATIC_SCRATCH_BYTES = 64 << 20
 
 def bf_gc_forward_static(plan, f, out, stream=None):
     """Forward with the library's fixed device scratch; allocates nothing (see bfgc.h)."""
-    _dev_f32(f, "f")
-    _dev_f32(out, "out")
+    px = _plan_px(plan)
+    _dev_f32(f, "f", px)
+    _dev_f32(out, "out", px)
     _check(lib().bf_gc_forward_static(plan, _ptr(f), _ptr(out), _stream(stream)), "bf_gc_forward_static")
     return out
 
 
 def bf_gc_backward(plan, f, gout, gf, gsigma_r, ws, stream=None):
+    """dL/df into gf (and dL/dsigma_r into gsigma_r, a one-element float64 CUDA tensor, or None)."""
+    px = _plan_px(plan)
+    _dev_f32(f, "f", px)
+    _dev_f32(gout, "gout", px)
+    _dev_f32(gf, "gf", px)
+    if gsigma_r is not None and not (isinstance(gsigma_r, torch.Tensor) and gsigma_r.is_cuda and
+                                     gsigma_r.dtype == torch.float64 and gsigma_r.numel() == 1):
+        raise ValueError("gsigma_r must be a one-element float64 CUDA tensor or None")
+    _dev_ws(ws)
     _check(lib().bf_gc_backward(plan, _ptr(f), _ptr(gout), _ptr(gf), _ptr(gsigma_r), _ptr(ws),
                                 ws.numel() * ws.element_size(), _stream(stream)), "bf_gc_backward")
     return gf
@@ -211,7 +236,8 @@ def bf_gc_diagnostics(plan, ws, stream=None):
     st = lib().bf_gc_diagnostics(plan, _ptr(ws), ctypes.byref(d), _stream(stream))
     if st not in (BF_OK, BF_ERR_TIMEOUT):
         _check(st, "bf_gc_diagnostics")
-    return {"n_guarded": d.n_guarded, "n_illcond": d.n_illcond, "error_flags": d.error_flags}
+    return {"n_guarded": d.n_guarded, "n_illcond": d.n_illcond, "error_flags": d.error_flags,
+            "n_refined": d.n_refined}
 
 
 def bf_gc_plan_destroy(plan):
@@ -256,7 +282,8 @@ def bf_gc_batch_forward(batch, fs, outs, ws, stream=None):
         raise ValueError("fs and outs differ in length")
     for f, o in zip(fs, outs):
         _dev_f32(f, "f")
-        _dev_f32(o, "out")
+        _dev_f32(o, "out", f.numel())
+    _dev_ws(ws)
     pf = (_P * len(fs))(*[t.data_ptr() for t in fs])
     po = (_P * len(outs))(*[t.data_ptr() for t in outs])
     _check(lib().bf_gc_batch_forward(batch, pf, po, _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
@@ -270,7 +297,7 @@ def bf_gc_batch_destroy(batch):
 
 def bf_direct(f, sigma_s, sigma_r, out=None, stream=None):
     _dev_f32(f, "f")
-    out = torch.empty_like(f) if out is None else _dev_f32(out, "out")
+    out = torch.empty_like(f) if out is None else _dev_f32(out, "out", f.numel())
     H, W = f.shape[-2], f.shape[-1]
     _check(lib().bf_direct(H, W, float(sigma_s), float(sigma_r), _ptr(f), _ptr(out), _stream(stream)),
            "bf_direct")

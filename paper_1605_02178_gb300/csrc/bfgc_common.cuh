@@ -15,6 +15,17 @@ __device__ __forceinline__ int mirror(int p, int n) {
     return q < n ? q : period - 1 - q;
 }
 
+// Decision of eq. (10) from the FP32 sums P, Q and Qa = sum |terms of Q|: 0 = divide
+// (conditioned), 1 = divide (ill-conditioned: |Q| < 1e-3 Qa, counted), 2 = guarded (output =
+// input), 3 = hand the pixel to the FP64 refinement (p.refine set).  See GcParams for the two
+// decision modes.
+__device__ __forceinline__ int ratio_decision(const GcParams& p, float P, float Q, float Qa) {
+    const bool bad = !(Qa > 0.0f) || !(Qa <= 3.0e38f) || !(fabsf(P) <= 3.0e38f);
+    if (p.refine) return (bad || !(fabsf(Q) >= p.flag_rel * Qa)) ? 3 : 0;
+    if (bad || !(fabsf(Q) >= p.guard_rel * Qa)) return 2;
+    return fabsf(Q) < (float)kIllcondRel * Qa ? 1 : 0;
+}
+
 // Per-pixel accumulation of eqs. (8)-(9) by Horner's rule in u = (f - t_c)/s_r over the
 // filtered channels Z_m, visited from m = N+1 down to 0:
 //   P = sum_{n=0}^{N} coef_n u^n Z_{n+1},  Q = sum_{n=0}^{N} coef_n u^n Z_n,
@@ -34,19 +45,28 @@ struct RatioAcc {
             Qa = fmaf(Qa, au, fabsf(q));
         }
     }
-    // Eq. (10) with the division guard; *how: 0 = conditioned, 1 = ill-conditioned
-    // (|Q| < 1e-3 Qa, counted), 2 = guarded (|Q| < 1e-12 Qa, non-finite, or all terms zero):
-    // the input pixel is returned.  The division is FP32 in every case: P and Q are FP32
-    // values, so their FP32 quotient is already correctly rounded.
+    // Eq. (10): *how = ratio_decision(...); the input pixel is returned when the pixel is
+    // guarded (2) or handed to the FP64 refinement (3, as a placeholder).  The FP32 division is
+    // correctly rounded for the FP32 P and Q.
     __device__ __forceinline__ float finish(const GcParams& p, float f, int* how) const {
-        if (!(fabsf(Q) >= 1e-12f * Qa) || !(Qa > 0.0f)) {
-            *how = 2;
-            return f;
-        }
-        *how = fabsf(Q) < 1e-3f * Qa ? 1 : 0;
-        return p.s_r * P / Q + p.t_c;
+        *how = ratio_decision(p, P, Q, Qa);
+        return *how >= 2 ? f : p.s_r * P / Q + p.t_c;
     }
 };
+
+// Append pixel i to the FP64 refinement list when `flag` is set.  Warp-aggregated: one
+// atomic per group of converged lanes; safe in divergent code (each converged group takes
+// its own slots).
+__device__ __forceinline__ void refine_push(const GcParams& p, DiagHeader* diag, bool flag, uint32_t i) {
+    const unsigned mask = __activemask();
+    const unsigned b = __ballot_sync(mask, flag);
+    if (!b) return;
+    const int lane = (int)(threadIdx.x & 31), leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(&diag->n_flagged, (unsigned long long)__popc(b));
+    base = __shfl_sync(mask, base, leader);
+    if (flag) p.refine[base + __popc(b & ((1u << lane) - 1u))] = i;
+}
 
 // Warp-aggregated update of the diagnostics counters.
 __device__ __forceinline__ void count_diag(DiagHeader* diag, unsigned guarded, unsigned illcond) {

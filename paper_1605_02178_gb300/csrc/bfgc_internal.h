@@ -15,12 +15,15 @@
 #define BF_TC_MAX_A 8        // tensor-core forms: R <= 16 * BF_TC_MAX_A
 #define BF_WS_HEADER 256     // bytes at the start of every workspace (diagnostics)
 
-// Diagnostics header at the start of a workspace.
+// Diagnostics header at the start of a workspace.  n_flagged is also the length of the
+// FP64 refinement list of the exact forms (see GcParams::refine).
 struct DiagHeader {
     unsigned long long n_guarded;
     unsigned long long n_illcond;
     unsigned int error_flags;
-    unsigned int pad[11];
+    unsigned int pad0;
+    unsigned long long n_flagged;
+    unsigned int pad[8];
 };
 
 // Per-plan scalars and coefficients, passed to kernels by value.
@@ -30,11 +33,45 @@ struct DiagHeader {
 // coef[n] = c~_n / kappa with c~_n = mu^n c_n, so that
 //   Q = sum_{n<=N} coef[n] u^n Fbar_n,  P = s_r sum_{n<=N} coef[n] u^n Fbar_{n+1}
 // differ from eqs. (8)-(9) only by the common factor kappa (cancels in P/Q).
+//
+// Division of eq. (10).  With `refine` set (the exact forms), a pixel whose FP32 sums give
+// |Q| < flag_rel * Qa (Qa = sum |terms of Q|), or no positive finite Qa, is not divided here:
+// its index is appended to the list `refine` (length in DiagHeader::n_flagged) and the pixel
+// is recomputed from f in FP64 by k_refine_fp64, which takes the guard decision and the
+// division in FP64.  flag_rel is at least 1e-3 and covers the storage precision's error in Q.
+// Without `refine` (the recursive form, and the adjoint), the decision is taken on the FP32
+// sums: output = input when |Q| < guard_rel * Qa or Qa is not positive and finite.
 struct GcParams {
     int H, W, N, C, R;
     float t_c, inv_sr, s_r, half_mu;
+    float flag_rel, guard_rel;
+    uint32_t* refine;
     float coef[BF_MAX_C];
 };
+
+// FP64 copy of the plan for the refinement kernel: u = (f - t_c) inv_sr, channels
+// exp(-half_mu u^2) u^n, coef[n] = c~_n / kappa, taps[d] = normalised g(d), d = 0..R.
+struct RefineParams {
+    int H, W, N, C, R;
+    double t_c, inv_sr, s_r, half_mu;
+    double coef[BF_MAX_C];
+    double taps[BF_MAX_R + 1];
+};
+
+// Relative guard of eq. (10) in FP64 (the oracle's delta) and the ill-conditioning mark.
+constexpr double kGuardRel64 = 1e-12;
+constexpr double kIllcondRel = 1e-3;
+// Refinement thresholds flag_rel by channel storage: FP32 (1e-3, the ill-conditioning mark);
+// BF16 and FP16, where the stored channels carry relative errors of up to a few times 2^-9
+// and 2^-11 (the stored row-pass output, and the 16-bit channels and taps of the banded
+// products), which reach Q at that size relative to the sum of its terms: 1/16 and 1/128, an
+// eightfold margin over four units of storage rounding.
+constexpr float kFlagRelFp32 = 1e-3f;
+constexpr float kFlagRelBf16 = 0.0625f;
+constexpr float kFlagRelFp16 = 0.0078125f;
+// Guard threshold where the decision is taken on FP32 sums: below 2^-17 Qa, Q is at the
+// level of the rounding error of the FP32 sums of about N terms.
+constexpr float kGuardRel32 = 7.62939453125e-6f;
 
 // Normalised 1-D spatial taps g[|d|], d = -R..R, sum over d equal to one.
 // (The paper's unnormalised g_s of Sec. I; the scale cancels in P/Q.)
@@ -70,6 +107,7 @@ struct bf_gc_plan_s {
     double dcoef_dsigma[BF_MAX_N + 1];  // d(c~_n)/d(sigma_r) / kappa
     GcParams gp;
     Taps taps;
+    RefineParams rp;     // FP64 plan of the refinement kernel
     Profiler prof;
 };
 
@@ -93,6 +131,10 @@ cudaError_t launch_build_hpass_f32(const float* f, float* Y, const GcParams& p, 
                                    cudaStream_t s);
 cudaError_t launch_vpass_combine_f32(const float* f, const float* Y, float* out, const GcParams& p, const Taps& t,
                                      size_t cs, DiagHeader* diag, cudaStream_t s);
+
+// FP64 recomputation of the listed pixels (k_refine.cu)
+cudaError_t launch_refine(const float* f, float* out, const uint32_t* list, DiagHeader* diag,
+                          const RefineParams& rp, cudaStream_t s);
 
 // exact filter of eq. (1)
 cudaError_t launch_direct(const float* f, float* out, int H, int W, int R, double sigma_s,

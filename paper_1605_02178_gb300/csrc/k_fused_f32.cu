@@ -302,6 +302,7 @@ k_vpass_combine_f32(const float* __restrict__ f, const float* __restrict__ Y, fl
             out[i] = a.finish(p, f[i], &how);
             guarded += how == 2;
             illcond += how == 1;
+            if (p.refine) refine_push(p, diag, how == 3, (uint32_t)i);
         }
     }
     count_diag(diag, guarded, illcond);

@@ -214,7 +214,8 @@ cudaError_t launch_vpass(const float* X, float* Y, const GcParams& p, const Taps
 
 // ---------------------------------------------------------------------------------------
 // Ratio: Horner in u over the channels (highest first), P and Q of eqs. (8)-(9) with the
-// rescaled coefficients, guarded division (eq. (10)), un-centring.
+// rescaled coefficients, the division of eq. (10) (guarded, or the pixel listed for the FP64
+// refinement; see GcParams), un-centring.
 __global__ void __launch_bounds__(256) k_combine(const float* __restrict__ f, const float* __restrict__ Z,
                                                  float* __restrict__ out, const GcParams p, size_t cs,
                                                  size_t px, DiagHeader* diag) {
@@ -243,14 +244,14 @@ __global__ void __launch_bounds__(256) k_combine(const float* __restrict__ f, co
             for (int k = 0; k < 4; ++k) acc[k].step(p, m, z[k]);
         }
         float o[4];
+        int how[4];
         unsigned guarded = 0, illcond = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            int how;
-            o[k] = acc[k].finish(p, fv[k], &how);
+            o[k] = acc[k].finish(p, fv[k], &how[k]);
             if (i0 + k < px) {
-                guarded += how == 2;
-                illcond += how == 1;
+                guarded += how[k] == 2;
+                illcond += how[k] == 1;
             }
         }
         if (full) {
@@ -260,6 +261,10 @@ __global__ void __launch_bounds__(256) k_combine(const float* __restrict__ f, co
                 if (i0 + k < px) out[i0 + k] = o[k];
         }
         count_diag(diag, guarded, illcond);
+        if (p.refine) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) refine_push(p, diag, i0 + k < px && how[k] == 3, (uint32_t)(i0 + k));
+        }
     }
 }
 

@@ -295,19 +295,26 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
                     }
                 }
             }
-            // eq. (10) with the division guard (see RatioAcc::finish; FP32 division), then the store
+            // eq. (10): divided in FP32, guarded, or listed for the FP64 refinement (ratio_decision)
             if (ok && y < p.H) {
                 float* orow = out + (size_t)y * p.W;
                 float o[16];
+                unsigned flagged = 0;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    if (!(fabsf(Q_[j]) >= 1e-12f * Qa[j]) || !(Qa[j] > 0.0f)) {
-                        o[j] = xb + j < p.W ? __ldg(f + (size_t)y * p.W + xb + j) : 0.0f;
-                        guarded += xb + j < p.W;
-                    } else {
-                        illcond += xb + j < p.W && fabsf(Q_[j]) < 1e-3f * Qa[j];
-                        o[j] = p.s_r * P_[j] / Q_[j] + p.t_c;
-                    }
+                    const int how = ratio_decision(p, P_[j], Q_[j], Qa[j]);
+                    const bool in = xb + j < p.W;
+                    if (how >= 2) o[j] = in ? __ldg(f + (size_t)y * p.W + xb + j) : 0.0f;
+                    else o[j] = p.s_r * P_[j] / Q_[j] + p.t_c;
+                    guarded += in && how == 2;
+                    illcond += in && how == 1;
+                    flagged |= (unsigned)(in && how == 3) << j;
+                }
+                // pixels for the FP64 refinement (none where the fit converges)
+                if (__any_sync(__activemask(), flagged != 0)) {
+#pragma unroll 1
+                    for (int j = 0; j < 16; ++j)
+                        refine_push(p, diag, (flagged >> j) & 1u, (uint32_t)((size_t)y * p.W + xb + j));
                 }
                 if (vec && xb + 16 <= p.W) {
 #pragma unroll

@@ -121,17 +121,36 @@ void refit(bf_gc_plan_s* p) {
     g.s_r = (float)p->s_r;
     g.half_mu = (float)(0.5 * p->mu);
     for (int n = 0; n < BF_MAX_C; ++n) g.coef[n] = n <= p->N ? (float)(p->c_tilde[n] / p->kappa) : 0.0f;
+    // decisions on the FP32 sums unless bf_gc_forward hands the pixel to the FP64 refinement
+    g.refine = nullptr;
+    g.flag_rel = kFlagRelFp32;
+    g.guard_rel = kGuardRel32;
+
+    RefineParams& r = p->rp;
+    r.H = p->H; r.W = p->W; r.N = p->N; r.C = p->C; r.R = p->R;
+    r.t_c = p->t_c;
+    r.inv_sr = 1.0 / p->s_r;
+    r.s_r = p->s_r;
+    r.half_mu = 0.5 * p->mu;
+    for (int n = 0; n < BF_MAX_C; ++n) r.coef[n] = n <= p->N ? p->c_tilde[n] / p->kappa : 0.0;
 }
 
-void make_taps(double sigma_s, int R, Taps* t) {
+void make_taps(double sigma_s, int R, Taps* t, double* t64) {
     double sum = 0.0;
     for (int d = -R; d <= R; ++d) sum += exp(-(double)d * d / (2.0 * sigma_s * sigma_s));
     t->R = R;
-    for (int d = 0; d <= BF_MAX_R; ++d)
-        t->g[d] = d <= R ? (float)(exp(-(double)d * d / (2.0 * sigma_s * sigma_s)) / sum) : 0.0f;
+    for (int d = 0; d <= BF_MAX_R; ++d) {
+        t64[d] = d <= R ? exp(-(double)d * d / (2.0 * sigma_s * sigma_s)) / sum : 0.0;
+        t->g[d] = (float)t64[d];
+    }
 }
 
-size_t fwd_workspace(const bf_gc_plan_s* p) {
+// The exact forms list pixels for the FP64 refinement; the recursive form (an IIR stand-in for
+// eq. (7), which a per-pixel window cannot reproduce) decides on its FP32 sums.
+bool refines(const bf_gc_plan_s* p) { return p->form != BF_FORM_RECURSIVE; }
+
+// Bytes of the forward workspace before the refinement list (header included).
+size_t fwd_body(const bf_gc_plan_s* p) {
     switch (p->form) {
     case BF_FORM_PLAIN:
         return BF_WS_HEADER + 2 * (size_t)p->C * bfgc::plain_plane_stride(p->H, p->W) * sizeof(float);
@@ -145,6 +164,14 @@ size_t fwd_workspace(const bf_gc_plan_s* p) {
     default:
         return 0;
     }
+}
+
+// Offset of the refinement list (one 32-bit pixel index per pixel at most) in the workspace.
+size_t refine_list_offset(const bf_gc_plan_s* p) { return round_up(fwd_body(p), 256); }
+
+size_t fwd_workspace(const bf_gc_plan_s* p) {
+    if (!refines(p)) return fwd_body(p);
+    return refine_list_offset(p) + round_up((size_t)p->H * p->W * sizeof(uint32_t), 256);
 }
 
 // Young and van Vliet (1995): scale q from sigma by their fit, b0..b3 cubic in q,
@@ -182,6 +209,8 @@ int auto_form(const bf_gc_plan_s* p) {
 }
 
 bool form_supported(const bf_gc_plan_s* p) {
+    // the refinement list holds 32-bit pixel indices
+    if (p->form != BF_FORM_RECURSIVE && (unsigned long long)p->H * p->W > 0xFFFFFFFFull) return false;
     switch (p->form) {
     case BF_FORM_PLAIN:
         return p->precision == BF_PREC_FP32;
@@ -259,7 +288,7 @@ bf_status bf_gc_plan(int H, int W, double sigma_s, double sigma_r, int N, bf_gc_
     p->form = BF_FORM_PLAIN; p->precision = BF_PREC_FP32; p->poly = BF_POLY_CHEBYSHEV; p->form_auto = false;
     p->save_channels = 0; p->tile_w = 0; p->used = false;
     refit(p);
-    make_taps(sigma_s, R, &p->taps);
+    make_taps(sigma_s, R, &p->taps, p->rp.taps);
     *out = p;
     return BF_OK;
 }
@@ -343,28 +372,37 @@ bf_status bf_gc_forward(bf_gc_plan_t p, const float* f, float* out, void* ws, si
     cudaError_t e = cudaMemsetAsync(diag, 0, sizeof(DiagHeader), s);
     if (e != cudaSuccess) return BF_ERR_CUDA;
     char* body = (char*)ws + BF_WS_HEADER;
+    // per-call parameters: the exact forms hand the pixels their FP32 sums cannot resolve to
+    // the FP64 refinement, through the list at the end of this workspace
+    GcParams gp = p->gp;
+    if (refines(p)) {
+        gp.refine = reinterpret_cast<uint32_t*>((char*)ws + refine_list_offset(p));
+        gp.flag_rel = p->precision == BF_PREC_BF16   ? kFlagRelBf16
+                      : p->precision == BF_PREC_FP16 ? kFlagRelFp16
+                                                     : kFlagRelFp32;
+    }
     switch (p->form) {
     case BF_FORM_PLAIN: {
         const size_t cs = bfgc::plain_plane_stride(p->H, p->W);
         float* X = (float*)body;
         float* Y = X + (size_t)p->C * cs;
         prof_mark(p, "build", s);
-        if ((e = bfgc::launch_build(f, X, p->gp, cs, s)) != cudaSuccess) break;
+        if ((e = bfgc::launch_build(f, X, gp, cs, s)) != cudaSuccess) break;
         prof_mark(p, "hpass", s);
-        if ((e = bfgc::launch_hpass(X, Y, p->gp, p->taps, cs, p->C, s)) != cudaSuccess) break;
+        if ((e = bfgc::launch_hpass(X, Y, gp, p->taps, cs, p->C, s)) != cudaSuccess) break;
         prof_mark(p, "vpass", s);
-        if ((e = bfgc::launch_vpass(Y, X, p->gp, p->taps, cs, p->C, s)) != cudaSuccess) break;
+        if ((e = bfgc::launch_vpass(Y, X, gp, p->taps, cs, p->C, s)) != cudaSuccess) break;
         prof_mark(p, "combine", s);
-        e = bfgc::launch_combine(f, X, out, p->gp, cs, diag, s);
+        e = bfgc::launch_combine(f, X, out, gp, cs, diag, s);
         break;
     }
     case BF_FORM_FUSED: {
         const size_t cs = bfgc::plain_plane_stride(p->H, p->W);
         float* Y = (float*)body;
         prof_mark(p, "build_hpass_f32", s);
-        if ((e = bfgc::launch_build_hpass_f32(f, Y, p->gp, p->taps, cs, s)) != cudaSuccess) break;
+        if ((e = bfgc::launch_build_hpass_f32(f, Y, gp, p->taps, cs, s)) != cudaSuccess) break;
         prof_mark(p, "vpass_combine_f32", s);
-        e = bfgc::launch_vpass_combine_f32(f, Y, out, p->gp, p->taps, cs, diag, s);
+        e = bfgc::launch_vpass_combine_f32(f, Y, out, gp, p->taps, cs, diag, s);
         break;
     }
     case BF_FORM_FUSED_TC: {
@@ -373,10 +411,10 @@ bf_status bf_gc_forward(bf_gc_plan_t p, const float* f, float* out, void* ws, si
         prof_mark(p, "build_hpass_tc", s);
         // row pass: the Toeplitz operand in tensor memory (default), or in shared memory with
         // the tile width the plan asks for
-        if ((e = p->tile_w ? bfgc::launch_build_hpass_umma(f, body, p->gp, p->taps, g, fp16, diag, s)
-                           : bfgc::launch_build_hpass_tc(f, body, p->gp, p->taps, g, fp16, diag, s)) != cudaSuccess) break;
+        if ((e = p->tile_w ? bfgc::launch_build_hpass_umma(f, body, gp, p->taps, g, fp16, diag, s)
+                           : bfgc::launch_build_hpass_tc(f, body, gp, p->taps, g, fp16, diag, s)) != cudaSuccess) break;
         prof_mark(p, "vpass_combine_tc", s);
-        e = bfgc::launch_vpass_combine_tc(f, body, out, p->gp, p->taps, g, fp16, diag, s);
+        e = bfgc::launch_vpass_combine_tc(f, body, out, gp, p->taps, g, fp16, diag, s);
         break;
     }
     case BF_FORM_RECURSIVE: {
@@ -386,17 +424,21 @@ bf_status bf_gc_forward(bf_gc_plan_t p, const float* f, float* out, void* ws, si
         float* tail = Y + (size_t)p->C * cs;
         const bfgc::IirCoef ic = iir_coefficients(p->sigma_s, p->R);
         prof_mark(p, "build", s);
-        if ((e = bfgc::launch_build(f, X, p->gp, cs, s)) != cudaSuccess) break;
+        if ((e = bfgc::launch_build(f, X, gp, cs, s)) != cudaSuccess) break;
         prof_mark(p, "iir_rows", s);
-        if ((e = bfgc::launch_iir(0, X, Y, tail, p->gp, ic, cs, p->C, s)) != cudaSuccess) break;   // result in X
+        if ((e = bfgc::launch_iir(0, X, Y, tail, gp, ic, cs, p->C, s)) != cudaSuccess) break;   // result in X
         prof_mark(p, "iir_cols", s);
-        if ((e = bfgc::launch_iir(1, X, Y, tail, p->gp, ic, cs, p->C, s)) != cudaSuccess) break;   // result in Y
+        if ((e = bfgc::launch_iir(1, X, Y, tail, gp, ic, cs, p->C, s)) != cudaSuccess) break;   // result in Y
         prof_mark(p, "combine", s);
-        e = bfgc::launch_combine(f, Y, out, p->gp, cs, diag, s);
+        e = bfgc::launch_combine(f, Y, out, gp, cs, diag, s);
         break;
     }
     default:
         return BF_ERR_UNSUPPORTED;
+    }
+    if (e == cudaSuccess && refines(p)) {
+        prof_mark(p, "refine_fp64", s);
+        e = bfgc::launch_refine(f, out, gp.refine, diag, p->rp, s);
     }
     prof_close(p, s);
     return cuda_status(e);
@@ -471,6 +513,7 @@ bf_status bf_gc_diagnostics(bf_gc_plan_t p, const void* ws, bf_gc_diag* out, bf_
     out->n_guarded = h.n_guarded;
     out->n_illcond = h.n_illcond;
     out->error_flags = h.error_flags;
+    out->n_refined = h.n_flagged;
     return h.error_flags ? BF_ERR_TIMEOUT : BF_OK;
 }
 

@@ -156,11 +156,17 @@ def test_bench_roofline_model_names_the_profiled_kernels():
     body = src[src.index("bf_status bf_gc_forward("):src.index("bf_status bf_gc_forward_host(")]
     forms = {"BF_FORM_PLAIN": "plain", "BF_FORM_FUSED": "fused", "BF_FORM_FUSED_TC": "fused_tc",
              "BF_FORM_RECURSIVE": "recursive"}
-    cases = re.split(r"\n\s*case (BF_FORM_[A-Z_]+): \{", body)
+    switch = body[body.index("switch (p->form) {"):body.index("default:")]
+    after = body[body.index("default:"):]
+    common = set(re.findall(r'prof_mark\(p, "(\w+)"', after))      # launched after every refining form
+    assert common == {"refine_fp64"}
+    cases = re.split(r"\n\s*case (BF_FORM_[A-Z_]+): \{", switch)
     seen = set()
     for enum_name, block in zip(cases[1::2], cases[2::2]):
         marks = set(re.findall(r'prof_mark\(p, "(\w+)"', block))
         form = forms[enum_name]
+        if form != "recursive":
+            marks |= common
         prec = "fp32" if form != "fused_tc" else "bf16"
         assert marks and marks == set(bench.kernel_model(form, prec, 22, 30)), form
         seen.add(form)

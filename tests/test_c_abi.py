@@ -30,10 +30,11 @@ int main(void) {
     CHECK(info.fit_err > 0.0 && info.fit_err < 1e-6);         /* sigma_r = 50, N = 20: converged */
     cs = ((size_t)2160 * 3840 + 63) / 64 * 64;
     CHECK(bf_gc_workspace_size(p, &fwd, &bwd) == BF_OK);
-    CHECK(fwd == 256 + 2 * 22 * cs * sizeof(float));          /* plain: two sets of FP32 planes */
+    /* plain: two sets of FP32 planes, then the FP64 refinement list (one index per pixel) */
+    CHECK(fwd == 256 + 2 * 22 * cs * sizeof(float) + (size_t)2160 * 3840 * 4);
     CHECK(bf_gc_plan_set(p, BF_OPT_FORM, BF_FORM_FUSED) == BF_OK);
     CHECK(bf_gc_workspace_size(p, &fwd, NULL) == BF_OK);
-    CHECK(fwd == 256 + 22 * cs * sizeof(float));              /* fused FP32: one set */
+    CHECK(fwd == 256 + 22 * cs * sizeof(float) + (size_t)2160 * 3840 * 4);   /* fused FP32: one set */
     CHECK(bf_gc_plan_set(p, BF_OPT_FORM, BF_FORM_AUTO) == BF_OK);
     CHECK(bf_gc_plan_info(p, &info) == BF_OK && info.form == BF_FORM_FUSED);   /* R = 30 <= 140 */
     CHECK(bf_gc_plan_set(p, BF_OPT_PRECISION, BF_PREC_BF16) == BF_OK);

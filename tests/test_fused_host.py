@@ -1,6 +1,7 @@
 """CPU checks of the fused FP32 form's host logic (BF_FORM_FUSED): option values, workspace
-size (one set of C FP32 channel planes, half of the plain form's two), and the argument
-checks that return before any CUDA call.  No kernel is launched here."""
+size (one set of C FP32 channel planes, half of the plain form's two, then the FP64
+refinement list of one 32-bit index per pixel), and the argument checks that return before
+any CUDA call.  No kernel is launched here."""
 import ctypes
 
 import pytest
@@ -18,8 +19,9 @@ def test_fused_workspace_is_one_set_of_planes(H, W, N):
     C = N + 2
     fused = GCPlan(H, W, 5.0, 30.0, N, form="fused").workspace_bytes()[0]
     plain = GCPlan(H, W, 5.0, 30.0, N, form="plain").workspace_bytes()[0]
-    assert fused == 256 + C * _plane(H, W) * 4
-    assert plain == 256 + 2 * C * _plane(H, W) * 4
+    lst = -(-H * W * 4 // 256) * 256
+    assert fused == 256 + C * _plane(H, W) * 4 + lst
+    assert plain == 256 + 2 * C * _plane(H, W) * 4 + lst
 
 
 def test_form_option_values():
