@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-equal-psnr", action="store_true", help="skip the sigma_r = 30, N = 28 block")
+    ap.add_argument("--no-backward", action="store_true", help="skip the backward leg")
     ap.add_argument("--forms", default=None, help="comma list of form:precision to run")
     ap.add_argument("--size", default=None, help="HxW instead of 2160x3840 (profiling cases)")
     ap.add_argument("--study", default=None, choices=["precision", "gpf", "batch", "sigma", "sweep"],
@@ -153,9 +155,23 @@ def kernel_model(form, precision, C, R):
         return {"build_hpass_f32": ("alu", 2 * (2 * R + 1) * C), "vpass_combine_f32": ("alu", 2 * (2 * R + 1) * C),
                 **refine}
     if form == "recursive":
-        return {"build": ("hbm", 4 + 4 * C), "iir_rows": ("hbm", 16 * C), "iir_cols": ("hbm", 16 * C),
+        # each recursive pass reads its C FP32 input planes and writes C output planes
+        return {"build": ("hbm", 4 + 4 * C), "iir_rows": ("hbm", 8 * C), "iir_cols": ("hbm", 8 * C),
                 "combine": ("hbm", 4 * C + 8)}
     return {"build_hpass_tc": ("hbm", 4 + s * C), "vpass_combine_tc": ("hbm", s * C + 8), **refine}
+
+
+def backward_model(C, R):
+    """Algorithmic work per pixel of the adjoint's kernels (bf_gc_backward, channels recomputed
+    by the plain FP32 form): ('hbm', bytes) or ('alu', flops)."""
+    return {"build": ("hbm", 4 + 4 * C), "hpass": ("alu", 2 * (2 * R + 1) * C),
+            "vpass": ("alu", 2 * (2 * R + 1) * C),
+            # reads the C filtered channels, f and dL/dout; writes C Lambda planes and D
+            "adjoint_lambda": ("hbm", 8 * C + 12),
+            # the transposed taps of eq. (7) (mirror images folded back), one pass per axis
+            "adjoint_vpass": ("alu", 2 * (2 * R + 1) * C), "adjoint_hpass": ("alu", 2 * (2 * R + 1) * C),
+            # reads f, the C planes K^T Lambda and D; writes dL/df
+            "adjoint_assemble": ("hbm", 4 * C + 12), "adjoint_reduce": ("hbm", 0)}
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -298,6 +314,20 @@ def run_ours(args):
                 acc["samples"] = int(idx.size)
             accuracy[f"{key[0]}/{key[1]}"] = acc
 
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    # ---- the paper's operating point (Sec. IV, Table 2: sigma_r = 30, N = 28), where every
+    # form's approximation error sits near the same PSNR against the exact filter: Mpixel/s of
+    # each form at (nearly) equal PSNR, and max-abs against the FP64 oracle at sampled pixels
+    equal = None
+    if rank == 0 and not args.no_equal_psnr:
+        equal = run_equal_psnr(args, dev, stream, base, f_np, inputs, outputs)
+
+    # ---- backward (the adjoint kernels behind bf_gc_backward)
+    backward = None
+    if rank == 0 and not args.no_backward:
+        backward = run_backward(args, dev, stream)
+
     # ---- end to end through the C ABI with host buffers (pinned), headline form: the
     # streaming call, every step uploading its image and downloading its result (consecutive
     # steps overlap); and the one-image synchronous call for reference
@@ -351,11 +381,11 @@ def run_ours(args):
     R = int(math.ceil(3 * SIGMA_S - 1e-9))
     model = kernel_model(headline[0], headline[1], C, R)
     kern = head["kernels"]
-    fp32_peak = 152 * 128 * 2 * ((head["clocks"] or {}).get("sm_mhz") or 2070.0) * 1e6 / 1e12
+    fp32_peak = sm_count * 128 * 2 * ((head["clocks"] or {}).get("sm_mhz") or 2070.0) * 1e6 / 1e12
 
     def form_entry(key, res):
         """value and per-kernel times of a form; for kernels bound by the FP32 ALUs, the achieved
-        FP32 rate (algorithmic flops) as a fraction of 152 SMs x 128 lanes x 2 flop x clock."""
+        FP32 rate (algorithmic flops) as a fraction of SMs x 128 lanes x 2 flop x clock."""
         e = {"value": res["value"], "ms_per_step": res["ms"],
              "kernels_ms_per_launch": {k: v[0] / max(1, v[1]) for k, v in res["kernels"].items()}}
         mdl = kernel_model(key[0], key[1], C, R)
@@ -377,12 +407,12 @@ def run_ours(args):
         else:
             achieved = per_px * px / (avg_ms * 1e-3) / 1e12
             sm_mhz = (head["clocks"] or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-            peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12   # FP32 FMA lanes x 2 flop x clock
+            peak = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12   # FP32 FMA lanes x 2 flop x clock
             unit = "TFLOP/s"
         tb = traffic_record(dominant)
         roofline = {"kernel": dominant, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                     "frac": achieved / peak, "peak_source": peak_kind if bound == "hbm" else
-                    "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load",
+                    f"{sm_count} SMs x 128 FP32 lanes x 2 flop x median SM clock under load",
                     "traffic": tb, "algorithmic_per_px": per_px, "avg_launch_ms": avg_ms}
     per_step_launches = sum(v[1] for v in kern.values()) / args.steps if kern else None
     line = {
@@ -404,12 +434,136 @@ def run_ours(args):
                 "d2h_bytes_per_step": px * 4, "api": "bf_gc_forward_host_stream (steps overlapped)",
                 "one_image_sync_value": world * px / e2e_sync_s / 1e6},
         "gpu_launches": int(round(per_step_launches * args.steps)) if per_step_launches else None,
-        "clocks": head["clocks"],
+        "clocks": dict(head["clocks"] or {}, sm_count=sm_count),
         "accuracy": accuracy,
+        "equal_psnr": equal,
+        "backward": backward,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def cuda_timed(fn, steps, warmup, stream):
+    """ms per call of fn() on `stream`, CUDA events around `steps` calls after `warmup`."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def profiled_kernels(plan_handle, fn, reps):
+    """{kernel: ms per launch} from the library's event profiler over `reps` calls of fn()."""
+    from paper_1605_02178_gb300 import bfgc
+    bfgc.bf_gc_profile_enable(plan_handle, True)
+    for _ in range(reps):
+        fn()
+    k = bfgc.bf_gc_profile_read(plan_handle)
+    bfgc.bf_gc_profile_enable(plan_handle, False)
+    return {name: ms / max(1, n) for name, (ms, n) in k.items()}
+
+
+def run_equal_psnr(args, dev, stream, base, f_np, inputs, outputs):
+    """4K image, sigma_s = 10, sigma_r = 30, N = 28 (the paper's Table 2 operating point): per
+    form ms, Mpixel/s, PSNR against the exact filter (bf_direct), max-abs against the FP64
+    oracle at 256 sampled pixels (4 corners + 252 seeded)."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_1605_02178_gb300 import api, bfgc
+    ss, sr, n = SIGMA_S, 30.0, 28
+    px = H * W
+    rng = np.random.default_rng(5)
+    idx = np.concatenate([[0, W - 1, (H - 1) * W, H * W - 1], rng.integers(0, H * W, 252)])
+    ref = oracle.gcf_at(f_np, idx, ss, sr, n)
+    exact = bfgc.bf_direct(base, ss, sr)
+    torch.cuda.synchronize(dev)
+    exact_np = exact.cpu().numpy().astype(np.float64)
+    res = {}
+    for form, prec in (("plain", "fp32"), ("fused", "fp32"), ("fused_tc", "fp16"), ("fused_tc", "bf16")):
+        plan = api.GCPlan(H, W, ss, sr, n, form=form, precision=prec)
+        ws = plan.workspace("fwd", dev)
+        state = {"i": 0}
+
+        def step():
+            i = state["i"] % N_INPUTS
+            plan.forward(inputs[i], outputs[i], ws, stream)
+            state["i"] += 1
+        ms = cuda_timed(step, args.steps, max(args.warmup, 3), stream)
+        kern = profiled_kernels(plan.handle, step, 3)
+        out = plan.forward(base, torch.empty_like(base), ws, stream)
+        torch.cuda.synchronize(dev)
+        o = out.cpu().numpy().astype(np.float64)
+        d = plan.diagnostics(ws, stream)
+        res[f"{form}/{prec}"] = {
+            "ms_per_step": ms, "mpixel_s": px / (ms * 1e-3) / 1e6, "kernels_ms_per_launch": kern,
+            "psnr_vs_exact_db": oracle.psnr_db(o, exact_np),
+            "maxabs_vs_fp64_oracle_sampled": float(np.abs(o.reshape(-1)[idx] - ref).max()),
+            "samples": int(idx.size), "n_refined": d["n_refined"], "n_guarded": d["n_guarded"]}
+        del plan, ws
+    return {"workload": f"uhd {W}x{H} edge+smooth field (seeded), sigma_s={ss}, sigma_r={sr}, N={n}",
+            "fit_err": api.GCPlan(8, 8, ss, sr, n).info["fit_err"],
+            "oracle_psnr_note": "all forms share the approximation error of the fit at N = 28",
+            "forms": res}
+
+
+def run_backward(args, dev, stream):
+    """dL/df and dL/dsigma_r (bf_gc_backward, channels recomputed) on the differentiation
+    workload (1024x1024 rectangles + noise 20, w ~ N(0, 1), sigma_s = 5, sigma_r = 25, N = 10)
+    and on the 4K workload (sigma_s = 10, sigma_r = 50, N = 20): ms, Mpixel/s and per-kernel
+    fractions of the roofline that bounds each kernel."""
+    import numpy as np
+    import torch
+    from paper_1605_02178_gb300 import api, synth
+    peaks, _ = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    out = {}
+    cases = (("diff_1024", synth.rects_image(1024, 1024, n_rects=20, noise_std=20.0, seed=2), 5.0, 25.0, 10),
+             ("uhd", synth.edge_smooth_image(H, W, noise_std=5.0, seed=1), SIGMA_S, SIGMA_R, N))
+    for name, f_np, ss, sr, n in cases:
+        h, w = f_np.shape
+        f = torch.from_numpy(f_np).to(dev)
+        gout = torch.from_numpy(np.random.default_rng(3).standard_normal((h, w)).astype(np.float32)).to(dev)
+        plan = api.GCPlan(h, w, ss, sr, n)
+        ws = plan.workspace("bwd", dev)
+        gf = torch.empty_like(f)
+        gs = torch.zeros((), dtype=torch.float64, device=dev)
+        from paper_1605_02178_gb300 import bfgc
+
+        def step():
+            bfgc.bf_gc_backward(plan.handle, f, gout, gf, gs, ws, stream)
+        ms = cuda_timed(step, args.steps, max(args.warmup, 3), stream)
+        kern = profiled_kernels(plan.handle, step, 3)
+        C, R = n + 2, int(math.ceil(3 * ss - 1e-9))
+        mdl = backward_model(C, R)
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        alu_peak = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+        roof = {}
+        for k, kms in kern.items():
+            bound, per_px = mdl.get(k, ("hbm", 0))
+            if not per_px:
+                continue
+            if bound == "hbm":
+                roof[k] = {"bound": "hbm", "achieved_gbs": per_px * h * w / (kms * 1e-3) / 1e9,
+                           "frac": per_px * h * w / (kms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+            else:
+                roof[k] = {"bound": "alu", "achieved_tflops": per_px * h * w / (kms * 1e-3) / 1e12,
+                           "frac": per_px * h * w / (kms * 1e-3) / 1e12 / alu_peak}
+        torch.cuda.synchronize(dev)
+        out[name] = {"shape": [h, w], "sigma_s": ss, "sigma_r": sr, "N": n, "ms_per_step": ms,
+                     "mpixel_s": h * w / (ms * 1e-3) / 1e6, "kernels_ms_per_launch": kern, "roofline": roof,
+                     "grad_finite": bool(torch.isfinite(gf).all()) and bool(torch.isfinite(gs))}
+        del plan, ws
+    out["note"] = (f"alu peak = {sm_count} SMs x 128 FP32 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz; "
+                   "hbm peak = measured copy bandwidth")
+    return out
 
 
 # --------------------------------------------------------------------------- studies
@@ -563,13 +717,22 @@ def run_sweep_study(args, dev):
             ms = e0.elapsed_time(e1) / 5
             o = out.cpu().numpy().astype(np.float64)
             d = plan.diagnostics(ws, stream)
-            print(json.dumps({
+            row = {
                 "study": "sweep", "image": "uhd 3840x2160", "sigma_s": ss, "sigma_r": sr, "N": N,
                 "form": form, "precision": prec, "fit_err": plan.info["fit_err"], "ms": ms,
                 "mpixel_s": H * W / (ms * 1e-3) / 1e6, "psnr_vs_exact_db": oracle.psnr_db(o, exn),
                 "maxabs_vs_fp64_oracle_sampled": float(np.abs(o.reshape(-1)[idx] - ref).max()),
                 "samples": int(idx.size), "n_guarded": d["n_guarded"], "n_illcond": d["n_illcond"],
-                "error_flags": d["error_flags"]}), flush=True)
+                "n_refined": d["n_refined"], "error_flags": d["error_flags"]}
+            if d["n_refined"]:
+                # the same form with the FP64 refinement off (BF_OPT_REFINE = 0)
+                p2 = api.GCPlan(H, W, ss, sr, N, form=form, precision=prec, refine=False)
+                w2 = p2.workspace("fwd", dev)
+                row["ms_refine_off"] = cuda_timed(lambda: p2.forward(ft, out, w2, stream), 5, 2, stream)
+                o2 = out.cpu().numpy().astype(np.float64)
+                row["maxabs_vs_fp64_oracle_sampled_refine_off"] = float(np.abs(o2.reshape(-1)[idx] - ref).max())
+                del p2, w2
+            print(json.dumps(row), flush=True)
             del plan, ws, out
 
 

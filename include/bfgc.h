@@ -62,12 +62,20 @@ enum {
                                  for bf_gc_backward to reuse; 0 = backward recomputes them.
                                  Plain form only: the other forms never hold the filtered
                                  channels as FP32 planes, and their backward recomputes them. */
-    BF_OPT_TILE_W = 7         /* value: row-pass kernel of the tensor-core form.  0 (default):
+    BF_OPT_TILE_W = 7,        /* value: row-pass kernel of the tensor-core form.  0 (default):
                                  Toeplitz operand in tensor memory, tiles of 128 output columns.
                                  64, 128 or 256: Toeplitz operand in shared memory, tiles of that
                                  many output columns (128 and 256 need ceil(R/16) <= 4, else
                                  BF_ERR_UNSUPPORTED).  The three widths give identical results;
                                  the default kernel sums the same products in another order. */
+    BF_OPT_REFINE = 8         /* value: 1 (default) = the exact forms recompute in FP64 the
+                                 pixels their own arithmetic cannot resolve and take the
+                                 division of eq. (10) there in FP64 (see bf_gc_diag); 0 = they
+                                 decide on their own sums like the recursive form (guarded
+                                 below 2^-17 Qa), with no second launch and no list in the
+                                 workspace.  Where the fit converges nothing is refined; where
+                                 it does not, up to a fifth of the pixels may be (BF16), each
+                                 costing a (2R+1)^2 window in FP64. */
 };
 enum {
     BF_FORM_PLAIN = 0,        /* 4 kernels: build F_n -> row filter -> column filter -> ratio; FP32 */

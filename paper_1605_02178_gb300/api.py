@@ -9,7 +9,7 @@ class GCPlan:
     """Owns a bf_gc_plan_t and its workspace tensors (allocated by PyTorch)."""
 
     def __init__(self, H, W, sigma_s, sigma_r, N, form="plain", precision="fp32", poly="chebyshev",
-                 L=0.0, U=255.0, save_channels=False, tile_w=0):
+                 L=0.0, U=255.0, save_channels=False, tile_w=0, refine=True):
         self.handle = B.bf_gc_plan(H, W, sigma_s, sigma_r, N)
         try:
             B.bf_gc_plan_set(self.handle, B.BF_OPT_FORM, B.FORMS[form])
@@ -22,6 +22,8 @@ class GCPlan:
             B.bf_gc_plan_set(self.handle, B.BF_OPT_SAVE_CHANNELS, 1 if save_channels else 0)
             if tile_w:
                 B.bf_gc_plan_set(self.handle, B.BF_OPT_TILE_W, int(tile_w))
+            if not refine:
+                B.bf_gc_plan_set(self.handle, B.BF_OPT_REFINE, 0)
         except Exception:
             B.bf_gc_plan_destroy(self.handle)
             self.handle = None

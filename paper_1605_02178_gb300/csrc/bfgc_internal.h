@@ -99,6 +99,7 @@ struct bf_gc_plan_s {
     int H, W, N, R, C;
     double sigma_s, sigma_r, L, U;
     int form, precision, poly, save_channels, tile_w;
+    int refine;          // BF_OPT_REFINE: FP64 refinement in the exact forms (default 1)
     bool form_auto;      // BF_FORM_AUTO was asked for: `form` is re-chosen on precision changes
     bool used;
     // derived (refit on option change)

@@ -145,9 +145,10 @@ void make_taps(double sigma_s, int R, Taps* t, double* t64) {
     }
 }
 
-// The exact forms list pixels for the FP64 refinement; the recursive form (an IIR stand-in for
-// eq. (7), which a per-pixel window cannot reproduce) decides on its FP32 sums.
-bool refines(const bf_gc_plan_s* p) { return p->form != BF_FORM_RECURSIVE; }
+// The exact forms list pixels for the FP64 refinement (unless BF_OPT_REFINE = 0); the
+// recursive form (an IIR stand-in for eq. (7), which a per-pixel window cannot reproduce)
+// decides on its FP32 sums.
+bool refines(const bf_gc_plan_s* p) { return p->form != BF_FORM_RECURSIVE && p->refine; }
 
 // Bytes of the forward workspace before the refinement list (header included).
 size_t fwd_body(const bf_gc_plan_s* p) {
@@ -210,7 +211,7 @@ int auto_form(const bf_gc_plan_s* p) {
 
 bool form_supported(const bf_gc_plan_s* p) {
     // the refinement list holds 32-bit pixel indices
-    if (p->form != BF_FORM_RECURSIVE && (unsigned long long)p->H * p->W > 0xFFFFFFFFull) return false;
+    if (refines(p) && (unsigned long long)p->H * p->W > 0xFFFFFFFFull) return false;
     switch (p->form) {
     case BF_FORM_PLAIN:
         return p->precision == BF_PREC_FP32;
@@ -286,7 +287,7 @@ bf_status bf_gc_plan(int H, int W, double sigma_s, double sigma_r, int N, bf_gc_
     p->sigma_s = sigma_s; p->sigma_r = sigma_r;
     p->L = 0.0; p->U = 255.0;
     p->form = BF_FORM_PLAIN; p->precision = BF_PREC_FP32; p->poly = BF_POLY_CHEBYSHEV; p->form_auto = false;
-    p->save_channels = 0; p->tile_w = 0; p->used = false;
+    p->save_channels = 0; p->tile_w = 0; p->refine = 1; p->used = false;
     refit(p);
     make_taps(sigma_s, R, &p->taps, p->rp.taps);
     *out = p;
@@ -325,6 +326,10 @@ bf_status bf_gc_plan_set(bf_gc_plan_t p, int option, double value) {
     case BF_OPT_SAVE_CHANNELS:
         if (iv != value || (iv != 0 && iv != 1)) return BF_ERR_INVALID_ARG;
         p->save_channels = iv;
+        return BF_OK;
+    case BF_OPT_REFINE:
+        if (iv != value || (iv != 0 && iv != 1)) return BF_ERR_INVALID_ARG;
+        p->refine = iv;
         return BF_OK;
     case BF_OPT_TILE_W:
         if (iv != value || (iv != 0 && iv != 64 && iv != 128 && iv != 256)) return BF_ERR_INVALID_ARG;

@@ -114,6 +114,26 @@ def test_recursive_form_guards_on_its_fp32_sums():
     assert sure.sum() <= d["n_guarded"] <= maybe.sum(), (sure.sum(), d["n_guarded"], maybe.sum())
 
 
+@pytest.mark.parametrize("form,prec", [("plain", "fp32"), ("fused_tc", "fp16")])
+def test_refinement_off_decides_on_the_forms_own_sums(form, prec):
+    """BF_OPT_REFINE = 0: no list and no second launch; the guard is taken on the form's own
+    sums at 2^-17 Qabs, like the recursive form."""
+    sr, N, ss = 8.0, 10, 2.0
+    f = guard_image(150, 200, seed=7)
+    ref, aux = oracle.gcf(f, ss, sr, N, return_pq=True)
+    r = ratio(aux)
+    plan = api.GCPlan(150, 200, ss, sr, N, form=form, precision=prec, refine=False)
+    on = api.GCPlan(150, 200, ss, sr, N, form=form, precision=prec)
+    assert plan.workspace_bytes()[0] < on.workspace_bytes()[0]          # no list
+    ws = plan.workspace("fwd")
+    out = plan.forward(torch.from_numpy(f).cuda(), ws=ws).cpu().numpy()
+    d = plan.diagnostics(ws)
+    assert d["n_refined"] == 0 and d["error_flags"] == 0
+    deep = aux["Qabs"] == 0.0                                           # every channel underflows
+    assert np.array_equal(out[deep], f[deep])
+    assert d["n_guarded"] >= deep.sum()
+
+
 def test_static_forward_refines_like_the_workspace_forward():
     """The allocation-free entry point runs the same forward, refinement included."""
     from paper_1605_02178_gb300 import bfgc
