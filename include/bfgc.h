@@ -142,9 +142,11 @@ typedef struct {
  * input pixel when |Q| < 1e-12 Qa or Qa = 0 ("guarded"), else P/Q + t_c.  FP32 cannot
  * resolve Q at 1e-12 Qa, so the exact forms (PLAIN, FUSED, FUSED_TC) take that decision in
  * FP64: a pixel whose sums in the form's own arithmetic give |Q| < r Qa (r = 1e-3 with FP32
- * channels, 1/16 with BF16, 1/128 with FP16: above the storage's error in Q) or non-finite
- * values is recomputed from the input image entirely in FP64 (eq. (7) as a window sum, the
- * channels, P, Q and Qa) and guarded or divided in FP64 ("refined").  Where the fit converges
+ * channels, 1/16 with BF16, 1/128 with FP16: above the storage's error in Q), a |Q| within
+ * the underflow error of the stored channels, or non-finite values is recomputed from the
+ * input image (eq. (7) as a window sum, the channels, P, Q and Qa): in FP64, where the guard
+ * and the division are then taken ("refined"); with 16-bit channels first in FP32, which
+ * settles the pixel when |Q| >= 1e-2 Qa there (the storage, not FP32, had been the limit).  Where the fit converges
  * no pixel comes near these thresholds and the refinement costs one empty launch.  The
  * RECURSIVE form (its spatial filter is an IIR, which a per-pixel window cannot reproduce)
  * decides on its FP32 sums: guarded when |Q| < 2^-17 Qa, the resolution of those sums. */
@@ -157,7 +159,10 @@ typedef struct {
                                        per step), bit 1: row pass with the Toeplitz operand in
                                        shared memory, bit 2: row pass with it in tensor memory,
                                        bit 3: column pass (channel pairs) */
-    unsigned long long n_refined;   /* pixels recomputed in FP64 (exact forms; 0 for RECURSIVE) */
+    unsigned long long n_refined;   /* pixels recomputed from the input (exact forms; 0 for RECURSIVE) */
+    unsigned long long n_refined_fp64; /* of those, the pixels recomputed and decided in FP64 (the
+                                       rest, in the BF16 / FP16 forms, were resolved by an FP32
+                                       recomputation: |Q| >= 1e-2 Qa there) */
 } bf_gc_diag;
 
 /* Create a plan for H x W images (Sec. III-B): fits, in FP64 on the host, the

@@ -41,7 +41,8 @@ class bf_gc_info(ctypes.Structure):
 
 class bf_gc_diag(ctypes.Structure):
     _fields_ = [("n_guarded", ctypes.c_ulonglong), ("n_illcond", ctypes.c_ulonglong),
-                ("error_flags", ctypes.c_uint), ("n_refined", ctypes.c_ulonglong)]
+                ("error_flags", ctypes.c_uint), ("n_refined", ctypes.c_ulonglong),
+                ("n_refined_fp64", ctypes.c_ulonglong)]
 
 
 class bf_kernel_time(ctypes.Structure):
@@ -237,7 +238,7 @@ def bf_gc_diagnostics(plan, ws, stream=None):
     if st not in (BF_OK, BF_ERR_TIMEOUT):
         _check(st, "bf_gc_diagnostics")
     return {"n_guarded": d.n_guarded, "n_illcond": d.n_illcond, "error_flags": d.error_flags,
-            "n_refined": d.n_refined}
+            "n_refined": d.n_refined, "n_refined_fp64": d.n_refined_fp64}
 
 
 def bf_gc_plan_destroy(plan):

@@ -15,13 +15,21 @@ __device__ __forceinline__ int mirror(int p, int n) {
     return q < n ? q : period - 1 - q;
 }
 
-// Decision of eq. (10) from the FP32 sums P, Q and Qa = sum |terms of Q|: 0 = divide
+// Decision of eq. (10) from the sums P, Q and Qa = sum |terms of Q| of a pixel at u: 0 = divide
 // (conditioned), 1 = divide (ill-conditioned: |Q| < 1e-3 Qa, counted), 2 = guarded (output =
 // input), 3 = hand the pixel to the FP64 refinement (p.refine set).  See GcParams for the two
-// decision modes.
-__device__ __forceinline__ int ratio_decision(const GcParams& p, float P, float Q, float Qa) {
+// decision modes.  In refinement mode a pixel is also handed over when |Q| is within the
+// absolute error of the stored channels (flag_abs = the few smallest normal values, or FP16's
+// subnormal spacing, times sum |coef_n| max(1, |u|)^N): there the channels have lost their
+// relative precision to underflow and the ratio |Q| / Qa says nothing.
+__device__ __forceinline__ int ratio_decision(const GcParams& p, float u, float P, float Q, float Qa) {
     const bool bad = !(Qa > 0.0f) || !(Qa <= 3.0e38f) || !(fabsf(P) <= 3.0e38f);
-    if (p.refine) return (bad || !(fabsf(Q) >= p.flag_rel * Qa)) ? 3 : 0;
+    if (p.refine) {
+        float tabs = p.flag_abs;
+        const float au = fabsf(u);
+        if (au > 1.0f) tabs *= __powf(au, (float)p.N);
+        return (bad || !(fabsf(Q) >= fmaf(p.flag_rel, Qa, tabs))) ? 3 : 0;
+    }
     if (bad || !(fabsf(Q) >= p.guard_rel * Qa)) return 2;
     return fabsf(Q) < (float)kIllcondRel * Qa ? 1 : 0;
 }
@@ -49,7 +57,7 @@ struct RatioAcc {
     // guarded (2) or handed to the FP64 refinement (3, as a placeholder).  The FP32 division is
     // correctly rounded for the FP32 P and Q.
     __device__ __forceinline__ float finish(const GcParams& p, float f, int* how) const {
-        *how = ratio_decision(p, P, Q, Qa);
+        *how = ratio_decision(p, u, P, Q, Qa);
         return *how >= 2 ? f : p.s_r * P / Q + p.t_c;
     }
 };

@@ -23,7 +23,8 @@ struct DiagHeader {
     unsigned int error_flags;
     unsigned int pad0;
     unsigned long long n_flagged;
-    unsigned int pad[8];
+    unsigned long long n_refined64;    // listed pixels that went on to the FP64 tier
+    unsigned int pad[6];
 };
 
 // Per-plan scalars and coefficients, passed to kernels by value.
@@ -39,24 +40,33 @@ struct DiagHeader {
 // its index is appended to the list `refine` (length in DiagHeader::n_flagged) and the pixel
 // is recomputed from f in FP64 by k_refine_fp64, which takes the guard decision and the
 // division in FP64.  flag_rel is at least 1e-3 and covers the storage precision's error in Q.
+// The test also refines pixels whose |Q| is within flag_abs max(1, |u|)^N of zero, where the
+// stored channels have lost their relative precision to underflow (see ratio_decision).
 // Without `refine` (the recursive form, and the adjoint), the decision is taken on the FP32
 // sums: output = input when |Q| < guard_rel * Qa or Qa is not positive and finite.
 struct GcParams {
     int H, W, N, C, R;
     float t_c, inv_sr, s_r, half_mu;
-    float flag_rel, guard_rel;
+    float flag_rel, flag_abs, guard_rel;
     uint32_t* refine;
     float coef[BF_MAX_C];
 };
 
-// FP64 copy of the plan for the refinement kernel: u = (f - t_c) inv_sr, channels
-// exp(-half_mu u^2) u^n, coef[n] = c~_n / kappa, taps[d] = normalised g(d), d = 0..R.
+// The plan for the refinement kernel (k_refine.cu), in FP64 and FP32: u = (f - t_c) inv_sr,
+// channels exp(-half_mu u^2) u^n, coef[n] = c~_n / kappa, taps[d] = normalised g(d), d = 0..R.
+// tier1: the form stores 16-bit channels, so a listed pixel is first recomputed in FP32 and
+// accepted there when |Q| >= tier1_rel Qa + abs32 max(1, |u|)^N.
 struct RefineParams {
     int H, W, N, C, R;
+    int tier1;
     double t_c, inv_sr, s_r, half_mu;
     double coef[BF_MAX_C];
     double taps[BF_MAX_R + 1];
+    float t_c32, inv_sr32, s_r32, half_mu32, tier1_rel, abs32;
+    float coef32[BF_MAX_C];
+    float taps32[BF_MAX_R + 1];
 };
+constexpr float kTier1Rel = 1e-2f;
 
 // Relative guard of eq. (10) in FP64 (the oracle's delta) and the ill-conditioning mark.
 constexpr double kGuardRel64 = 1e-12;
@@ -69,6 +79,13 @@ constexpr double kIllcondRel = 1e-3;
 constexpr float kFlagRelFp32 = 1e-3f;
 constexpr float kFlagRelBf16 = 0.0625f;
 constexpr float kFlagRelFp16 = 0.0078125f;
+// Absolute part of the refinement test, per unit of sum_n |coef_n| (see ratio_decision): FP32
+// and BF16 channels lose relative precision below the smallest normal value 2^-126, so a Q
+// within 2^-123 is refined; FP16 channels (stored times 2^14, in which units the sums are
+// taken) have a subnormal spacing of 2^-24, which is four units of FP16 rounding (2^-12)
+// relative to 2^-11.
+constexpr float kFlagAbsFp32 = 9.4039548065783e-38f;   // 2^-123
+constexpr float kFlagAbsFp16 = 4.8828125e-4f;          // 2^-11
 // Guard threshold where the decision is taken on FP32 sums: below 2^-17 Qa, Q is at the
 // level of the rounding error of the FP32 sums of about N terms.
 constexpr float kGuardRel32 = 7.62939453125e-6f;

@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_vpass_combine_pairs(
                 unsigned flagged = 0;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const int how = ratio_decision(p, P_[j], Q_[j], Qa[j]);
+                    const int how = ratio_decision(p, u[j], P_[j], Q_[j], Qa[j]);
                     const bool in = xb + j < p.W;
                     if (how >= 2) o[j] = in ? __ldg(f + (size_t)y * p.W + xb + j) : 0.0f;
                     else o[j] = p.s_r * P_[j] / Q_[j] + p.t_c;

@@ -295,6 +295,8 @@ k_vpass_combine_f32(const float* __restrict__ f, const float* __restrict__ Y, fl
         if (y < H && x < W) {
             const size_t i = (size_t)y * W + x;
             RatioAcc a;
+            a.u = us[(rb + v) * FC_COLS + c];
+            a.au = fabsf(a.u);
             a.P = P[v];
             a.Q = Q[v];
             a.Qa = Qa[v];

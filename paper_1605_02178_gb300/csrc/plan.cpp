@@ -124,6 +124,7 @@ void refit(bf_gc_plan_s* p) {
     // decisions on the FP32 sums unless bf_gc_forward hands the pixel to the FP64 refinement
     g.refine = nullptr;
     g.flag_rel = kFlagRelFp32;
+    g.flag_abs = 0.0f;
     g.guard_rel = kGuardRel32;
 
     RefineParams& r = p->rp;
@@ -133,15 +134,28 @@ void refit(bf_gc_plan_s* p) {
     r.s_r = p->s_r;
     r.half_mu = 0.5 * p->mu;
     for (int n = 0; n < BF_MAX_C; ++n) r.coef[n] = n <= p->N ? p->c_tilde[n] / p->kappa : 0.0;
+    r.t_c32 = g.t_c;
+    r.inv_sr32 = g.inv_sr;
+    r.s_r32 = g.s_r;
+    r.half_mu32 = g.half_mu;
+    r.tier1_rel = kTier1Rel;
+    double a1 = 0.0;
+    for (int n = 0; n < BF_MAX_C; ++n) {
+        r.coef32[n] = g.coef[n];
+        a1 += fabs((double)g.coef[n]);
+    }
+    r.abs32 = (float)(kFlagAbsFp32 * a1);
+    r.tier1 = 0;                                   // set per call from the storage precision
 }
 
-void make_taps(double sigma_s, int R, Taps* t, double* t64) {
+void make_taps(double sigma_s, int R, Taps* t, double* t64, float* t32) {
     double sum = 0.0;
     for (int d = -R; d <= R; ++d) sum += exp(-(double)d * d / (2.0 * sigma_s * sigma_s));
     t->R = R;
     for (int d = 0; d <= BF_MAX_R; ++d) {
         t64[d] = d <= R ? exp(-(double)d * d / (2.0 * sigma_s * sigma_s)) / sum : 0.0;
         t->g[d] = (float)t64[d];
+        t32[d] = t->g[d];
     }
 }
 
@@ -289,7 +303,7 @@ bf_status bf_gc_plan(int H, int W, double sigma_s, double sigma_r, int N, bf_gc_
     p->form = BF_FORM_PLAIN; p->precision = BF_PREC_FP32; p->poly = BF_POLY_CHEBYSHEV; p->form_auto = false;
     p->save_channels = 0; p->tile_w = 0; p->refine = 1; p->used = false;
     refit(p);
-    make_taps(sigma_s, R, &p->taps, p->rp.taps);
+    make_taps(sigma_s, R, &p->taps, p->rp.taps, p->rp.taps32);
     *out = p;
     return BF_OK;
 }
@@ -385,6 +399,9 @@ bf_status bf_gc_forward(bf_gc_plan_t p, const float* f, float* out, void* ws, si
         gp.flag_rel = p->precision == BF_PREC_BF16   ? kFlagRelBf16
                       : p->precision == BF_PREC_FP16 ? kFlagRelFp16
                                                      : kFlagRelFp32;
+        double a1 = 0.0;                                   // sum_n |coef_n|
+        for (int n = 0; n <= p->N; ++n) a1 += fabs((double)gp.coef[n]);
+        gp.flag_abs = (float)((p->precision == BF_PREC_FP16 ? kFlagAbsFp16 : kFlagAbsFp32) * a1);
     }
     switch (p->form) {
     case BF_FORM_PLAIN: {
@@ -443,7 +460,9 @@ bf_status bf_gc_forward(bf_gc_plan_t p, const float* f, float* out, void* ws, si
     }
     if (e == cudaSuccess && refines(p)) {
         prof_mark(p, "refine_fp64", s);
-        e = bfgc::launch_refine(f, out, gp.refine, diag, p->rp, s);
+        RefineParams rp = p->rp;
+        rp.tier1 = p->precision != BF_PREC_FP32;
+        e = bfgc::launch_refine(f, out, gp.refine, diag, rp, s);
     }
     prof_close(p, s);
     return cuda_status(e);
@@ -519,6 +538,7 @@ bf_status bf_gc_diagnostics(bf_gc_plan_t p, const void* ws, bf_gc_diag* out, bf_
     out->n_illcond = h.n_illcond;
     out->error_flags = h.error_flags;
     out->n_refined = h.n_flagged;
+    out->n_refined_fp64 = h.n_refined64;
     return h.error_flags ? BF_ERR_TIMEOUT : BF_OK;
 }
 

@@ -7,7 +7,8 @@ recomputed from the input in FP64 (n_refined).  So, with r = |Q|/Qabs from the o
   * pixels with Qabs = 0 or r < 1e-14 are guarded on the GPU: output = input, bit for bit;
   * pixels with r > 1e-9 are not: n_guarded lies between the two oracle counts;
   * refined pixels (surely those with r far below the form's flag threshold) match the
-    oracle's output to 1e-3 although they are ill-conditioned;
+    oracle's output to 1e-3 although they are ill-conditioned: in FP64 below 1e-2 (and
+    always for the FP32 forms), in FP32 from the input above it (the 16-bit forms);
   * n_illcond (FP64 for refined pixels) lies between the oracle's counts at 0.9e-3 and 1.1e-3.
 The recursive form decides on its FP32 sums (guarded below 2^-17 Qabs, their resolution), so
 it is held to the bands r < 1e-8 (guarded) and r > 1e-4 (not guarded) against its twin.
@@ -69,6 +70,11 @@ def test_exact_forms_guard_like_the_oracle(form, prec, flag, H, W, ss):
     assert sure.sum() >= 20
     # (more are refined where the form's channels underflow, e.g. FP32 at |u| > 0.84 when sigma_r = 8)
     assert d["n_refined"] >= (r < flag / 8).sum()
+    # the FP64 tier takes every listed pixel of the FP32 forms, and of the 16-bit forms those an
+    # FP32 recomputation leaves below 1e-2 Qabs
+    assert d["n_refined_fp64"] >= ((r < 5e-3) | (aux["Qabs"] == 0.0)).sum()
+    if prec == "fp32":
+        assert d["n_refined_fp64"] == d["n_refined"]
     err = np.abs(out.astype(np.float64) - ref)
     Q = np.maximum(np.abs(aux["Q"]), 1e-300)
     # both sides in FP64: within the first-order rounding bound of P/Q at FP64 (with margin)
@@ -77,6 +83,12 @@ def test_exact_forms_guard_like_the_oracle(form, prec, flag, H, W, ss):
     lo = ((r < 0.9e-3) & ~loose).sum()
     hi = ((r < 1.1e-3) & ~loose).sum()
     assert lo <= d["n_illcond"] <= hi, (lo, d["n_illcond"], hi)
+    if prec == "bf16":
+        # listed and settled by the FP32 recomputation: within its first-order rounding bound
+        mid = (r >= 2e-2) & (r < flag / 2)
+        assert mid.sum() >= 20
+        bound32 = 1e-5 * (aux["Pabs"] + np.abs(aux["P"]) / Q * aux["Qabs"]) / Q + 1e-3
+        assert np.all(err[mid] <= bound32[mid]), float(np.max(err[mid] - bound32[mid]))
     if prec == "fp32":
         # the rest is divided in FP32: within the first-order rounding bound of P/Q
         bound = 4e-6 * (aux["Pabs"] + np.abs(aux["P"]) / Q * aux["Qabs"]) / Q + 1e-3
