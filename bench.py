@@ -165,7 +165,7 @@ def backward_model(C, R):
     """Algorithmic work per pixel of the adjoint's kernels (bf_gc_backward, channels recomputed
     by the plain FP32 form): ('hbm', bytes) or ('alu', flops)."""
     return {"build": ("hbm", 4 + 4 * C), "hpass": ("alu", 2 * (2 * R + 1) * C),
-            "vpass": ("alu", 2 * (2 * R + 1) * C),
+            "build_hpass_f32": ("alu", 2 * (2 * R + 1) * C), "vpass": ("alu", 2 * (2 * R + 1) * C),
             # reads the C filtered channels, f and dL/dout; writes C Lambda planes and D
             "adjoint_lambda": ("hbm", 8 * C + 12),
             # the transposed taps of eq. (7) (mirror images folded back), one pass per axis

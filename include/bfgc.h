@@ -68,7 +68,7 @@ enum {
                                  many output columns (128 and 256 need ceil(R/16) <= 4, else
                                  BF_ERR_UNSUPPORTED).  The three widths give identical results;
                                  the default kernel sums the same products in another order. */
-    BF_OPT_REFINE = 8         /* value: 1 (default) = the exact forms recompute in FP64 the
+    BF_OPT_REFINE = 8,        /* value: 1 (default) = the exact forms recompute in FP64 the
                                  pixels their own arithmetic cannot resolve and take the
                                  division of eq. (10) there in FP64 (see bf_gc_diag); 0 = they
                                  decide on their own sums like the recursive form (guarded
@@ -76,6 +76,16 @@ enum {
                                  workspace.  Where the fit converges nothing is refined; where
                                  it does not, up to a fifth of the pixels may be (BF16), each
                                  costing a (2R+1)^2 window in FP64. */
+    BF_OPT_WAIT_US = 9,       /* value: bound, in microseconds, of one wait of a pipelined
+                                 tensor-core kernel on another role (1 .. 1e7; default 1e6).  A
+                                 wait that runs out sets a bit of bf_gc_diag.error_flags (then
+                                 BF_ERR_TIMEOUT from bf_gc_diagnostics) and every role of the
+                                 kernel returns; the output of that call is incomplete. */
+    BF_OPT_STALL = 10         /* value: 0 (default).  For testing the bounded waits only: 1 = the
+                                 tensor-core row pass never hands its first tile to the MMA
+                                 issuer, 2 = the tensor-core column pass never loads its first
+                                 stage, so that a wait runs out (BF_ERR_TIMEOUT) without any
+                                 asynchronous copy or MMA left outstanding. */
 };
 enum {
     BF_FORM_PLAIN = 0,        /* 4 kernels: build F_n -> row filter -> column filter -> ratio; FP32 */

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libbfgc.so")
 BF_OK, BF_ERR_INVALID_ARG, BF_ERR_UNSUPPORTED, BF_ERR_NOMEM, BF_ERR_CUDA, BF_ERR_TIMEOUT, \
     BF_ERR_RANGE, BF_ERR_WORKSPACE = range(8)
 BF_OPT_FORM, BF_OPT_PRECISION, BF_OPT_RANGE_L, BF_OPT_RANGE_U, BF_OPT_POLY, BF_OPT_SAVE_CHANNELS, \
-    BF_OPT_TILE_W, BF_OPT_REFINE = range(1, 9)
+    BF_OPT_TILE_W, BF_OPT_REFINE, BF_OPT_WAIT_US, BF_OPT_STALL = range(1, 11)
 BF_FORM_PLAIN, BF_FORM_FUSED_TC, BF_FORM_RECURSIVE, BF_FORM_AUTO, BF_FORM_FUSED = range(5)
 BF_AUTO_FP32_EXACT_MAX_R = 140
 BF_PREC_FP32, BF_PREC_BF16, BF_PREC_FP16 = range(3)

@@ -15,8 +15,6 @@ struct AdjCoef {
 
 cudaError_t launch_adjoint_lambda(const float* f, const float* gout, const float* Z, float* Lam, float* Dterm,
                                   double* partial, const GcParams& p, const AdjCoef& ac, size_t cs, cudaStream_t s);
-cudaError_t launch_adjoint_pass(int axis, const float* X, float* Y, const GcParams& p, const Taps& t, size_t cs,
-                                int planes, cudaStream_t s);
 cudaError_t launch_adjoint_assemble(const float* f, const float* Mch, const float* Dterm, float* gf, double* partial,
                                     const GcParams& p, const AdjCoef& ac, size_t cs, cudaStream_t s);
 cudaError_t launch_adjoint_reduce(const double* partial, int n, double* out, cudaStream_t s);

@@ -19,19 +19,20 @@ __device__ __forceinline__ int mirror(int p, int n) {
 // (conditioned), 1 = divide (ill-conditioned: |Q| < 1e-3 Qa, counted), 2 = guarded (output =
 // input), 3 = hand the pixel to the FP64 refinement (p.refine set).  See GcParams for the two
 // decision modes.  In refinement mode a pixel is also handed over when |Q| is within the
-// absolute error of the stored channels (flag_abs = the few smallest normal values, or FP16's
-// subnormal spacing, times sum |coef_n| max(1, |u|)^N): there the channels have lost their
-// relative precision to underflow and the ratio |Q| / Qa says nothing.
+// absolute error that underflow of the stored channels can bring into Q: flag_abs (16 half
+// spacings of the storage's smallest values) times A(|u|) = sum_n |coef_n| |u|^n, bounded by
+// |coef_0| + |u| sum_n |coef_n| for |u| <= 1 and by sum_n |coef_n| |u|^N beyond.
 __device__ __forceinline__ int ratio_decision(const GcParams& p, float u, float P, float Q, float Qa) {
     const bool bad = !(Qa > 0.0f) || !(Qa <= 3.0e38f) || !(fabsf(P) <= 3.0e38f);
+    const float lhs = fabsf(Q);
     if (p.refine) {
-        float tabs = p.flag_abs;
         const float au = fabsf(u);
-        if (au > 1.0f) tabs *= __powf(au, (float)p.N);
-        return (bad || !(fabsf(Q) >= fmaf(p.flag_rel, Qa, tabs))) ? 3 : 0;
+        const float bound = au <= 1.0f ? fmaf(au, p.flag_abs_sum, p.flag_abs * fabsf(p.coef[0]))
+                                       : p.flag_abs_sum * __powf(au, (float)p.N);
+        return (bad || !(lhs >= fmaf(p.flag_rel, Qa, bound))) ? 3 : 0;
     }
-    if (bad || !(fabsf(Q) >= p.guard_rel * Qa)) return 2;
-    return fabsf(Q) < (float)kIllcondRel * Qa ? 1 : 0;
+    if (bad || !(lhs >= p.guard_rel * Qa)) return 2;
+    return lhs < (float)kIllcondRel * Qa ? 1 : 0;
 }
 
 // Per-pixel accumulation of eqs. (8)-(9) by Horner's rule in u = (f - t_c)/s_r over the

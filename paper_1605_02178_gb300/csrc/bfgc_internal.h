@@ -40,22 +40,28 @@ struct DiagHeader {
 // its index is appended to the list `refine` (length in DiagHeader::n_flagged) and the pixel
 // is recomputed from f in FP64 by k_refine_fp64, which takes the guard decision and the
 // division in FP64.  flag_rel is at least 1e-3 and covers the storage precision's error in Q.
-// The test also refines pixels whose |Q| is within flag_abs max(1, |u|)^N of zero, where the
-// stored channels have lost their relative precision to underflow (see ratio_decision).
+// The test also refines pixels whose |Q| is within flag_abs sum_n |coef_n| |u|^n of zero (the
+// error that underflow of the stored channels can bring; flag_abs_sum = flag_abs sum_n |coef_n|),
+// see ratio_decision.
 // Without `refine` (the recursive form, and the adjoint), the decision is taken on the FP32
 // sums: output = input when |Q| < guard_rel * Qa or Qa is not positive and finite.
 struct GcParams {
     int H, W, N, C, R;
     float t_c, inv_sr, s_r, half_mu;
-    float flag_rel, flag_abs, guard_rel;
+    float flag_rel, flag_abs, flag_abs_sum, guard_rel;
     uint32_t* refine;
+    // bound of one pipeline wait in the tensor-core kernels (BF_OPT_WAIT_US), and the test-only
+    // stall of BF_OPT_STALL (0: none; 1: the row pass's first build group withholds its first
+    // tile; 2: the column pass's TMA producer withholds its first stage)
+    unsigned long long wait_ns;
+    int stall;
     float coef[BF_MAX_C];
 };
 
 // The plan for the refinement kernel (k_refine.cu), in FP64 and FP32: u = (f - t_c) inv_sr,
 // channels exp(-half_mu u^2) u^n, coef[n] = c~_n / kappa, taps[d] = normalised g(d), d = 0..R.
 // tier1: the form stores 16-bit channels, so a listed pixel is first recomputed in FP32 and
-// accepted there when |Q| >= tier1_rel Qa + abs32 max(1, |u|)^N.
+// accepted there when |Q| >= tier1_rel Qa + abs32 sum_n |coef_n| |u|^n.
 struct RefineParams {
     int H, W, N, C, R;
     int tier1;
@@ -79,13 +85,13 @@ constexpr double kIllcondRel = 1e-3;
 constexpr float kFlagRelFp32 = 1e-3f;
 constexpr float kFlagRelBf16 = 0.0625f;
 constexpr float kFlagRelFp16 = 0.0078125f;
-// Absolute part of the refinement test, per unit of sum_n |coef_n| (see ratio_decision): FP32
-// and BF16 channels lose relative precision below the smallest normal value 2^-126, so a Q
-// within 2^-123 is refined; FP16 channels (stored times 2^14, in which units the sums are
-// taken) have a subnormal spacing of 2^-24, which is four units of FP16 rounding (2^-12)
-// relative to 2^-11.
+// Absolute part of the refinement test, per unit of sum_n |coef_n| |u|^n (see ratio_decision):
+// FP32 and BF16 channels lose relative precision below the smallest normal value 2^-126, so a
+// Q within 2^-123 is refined; FP16 channels (stored times 2^14, the units in which the sums are
+// taken) round with an absolute error of up to 2^-25 near zero, and a Q within 16 such errors
+// (2^-21) is refined.
 constexpr float kFlagAbsFp32 = 9.4039548065783e-38f;   // 2^-123
-constexpr float kFlagAbsFp16 = 4.8828125e-4f;          // 2^-11
+constexpr float kFlagAbsFp16 = 4.76837158203125e-7f;   // 2^-21
 // Guard threshold where the decision is taken on FP32 sums: below 2^-17 Qa, Q is at the
 // level of the rounding error of the FP32 sums of about N terms.
 constexpr float kGuardRel32 = 7.62939453125e-6f;
@@ -117,6 +123,8 @@ struct bf_gc_plan_s {
     double sigma_s, sigma_r, L, U;
     int form, precision, poly, save_channels, tile_w;
     int refine;          // BF_OPT_REFINE: FP64 refinement in the exact forms (default 1)
+    double wait_us;      // BF_OPT_WAIT_US
+    int stall;           // BF_OPT_STALL (testing the bounded waits)
     bool form_auto;      // BF_FORM_AUTO was asked for: `form` is re-chosen on precision changes
     bool used;
     // derived (refit on option change)
@@ -141,6 +149,11 @@ cudaError_t launch_vpass(const float* X, float* Y, const GcParams& p, const Taps
                          int planes, cudaStream_t s);
 cudaError_t launch_combine(const float* f, const float* Z, float* out, const GcParams& p,
                            size_t cs, DiagHeader* diag, cudaStream_t s);
+// adjoints of the row and column passes (zero extension, mirror images folded back)
+cudaError_t launch_hpass_adjoint(const float* X, float* Y, const GcParams& p, const Taps& t, size_t cs,
+                                 int planes, cudaStream_t s);
+cudaError_t launch_vpass_adjoint(const float* X, float* Y, const GcParams& p, const Taps& t, size_t cs,
+                                 int planes, cudaStream_t s);
 
 // fused FP32 form: (build + row pass) -> C row-filtered planes of stride cs -> (column pass +
 // ratio); false / cudaErrorInvalidValue where its shared-memory windows do not fit (large R)

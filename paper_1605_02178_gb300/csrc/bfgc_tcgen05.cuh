@@ -10,7 +10,8 @@
 namespace bfgc {
 namespace tc {
 
-constexpr unsigned kWaitNs = 1000000000u;        // bound of one mbarrier wait (1 s)
+constexpr unsigned kWaitNs = 1000000000u;        // bound of a drain wait, and the default bound of
+                                                 // a pipeline wait (GcParams::wait_ns)
 // Taps staged in shared memory for the Toeplitz fills: the lanes of a warp read different taps,
 // and reading them from the kernel-parameter bank serialises (one access per distinct address)
 constexpr int kTapsSmem = 132;                   // >= R + 1 for R <= 128 (ceil(R/16) <= 8)
@@ -54,15 +55,15 @@ __device__ __forceinline__ uint64_t global_ns() {
 // Wait for the phase of parity `parity` of `bar` (every waiter walks its barrier's phases in
 // order, so the phase before the awaited one is complete).  Gives up when another role raised
 // the abort flag, or (raising it, and or-ing `flag` into the workspace's error flags) after
-// kWaitNs.
+// `limit_ns` nanoseconds.
 __device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, unsigned parity, volatile int* abort_flag,
-                                                DiagHeader* diag, unsigned flag) {
+                                                DiagHeader* diag, unsigned flag, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (global_ns() - t0 > kWaitNs) break;
+        if (global_ns() - t0 > limit_ns) break;
     }
     *abort_flag = 1;
     atomicOr(&diag->error_flags, flag);
@@ -70,14 +71,14 @@ __device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, unsigned parity, 
 }
 // As mbar_wait_abort, polling without the suspend hint
 __device__ __forceinline__ bool mbar_wait_abort_poll(uint64_t* bar, unsigned parity, volatile int* abort_flag,
-                                                     DiagHeader* diag, unsigned flag) {
+                                                     DiagHeader* diag, unsigned flag, uint64_t limit_ns) {
     if (mbar_poll(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (unsigned i = 0;; ++i) {
         if (mbar_poll(bar, parity)) return true;
         if ((i & 15) == 15) {
             if (*abort_flag) return false;
-            if (global_ns() - t0 > kWaitNs) break;
+            if (global_ns() - t0 > limit_ns) break;
         }
     }
     *abort_flag = 1;
@@ -153,6 +154,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* z) {
                  : "r"(taddr) : "memory");
 #pragma unroll
     for (int j = 0; j < 16; ++j) z[j] = __uint_as_float(v[j]);
+}
+// Split-phase load of 8 consecutive 32-bit columns of this warp's 32 lanes: tmem_ld8_start
+// issues it, tmem_wait8 waits for every load of the thread issued so far.  The registers pass
+// through the wait (in-out operands), so no use of them can be scheduled before it; between the
+// two the thread can compute on registers of an earlier load.
+__device__ __forceinline__ void tmem_ld8_start(uint32_t taddr, uint32_t* v) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr) : "memory");
+}
+__device__ __forceinline__ void tmem_wait8(uint32_t* v) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7])
+                 :: "memory");
 }
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* r) {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n"

@@ -7,7 +7,8 @@
 // Given w = dL/dout:
 //   Lambda_m = w s_r/Q (coef_{m-1} u^{m-1} [m >= 1] - (P/Q) coef_m u^m [m <= N])   (dL/dFbar_m)
 //   D        = w s_r/Q (sum n coef_n u^{n-1} Fbar_{n+1} - (P/Q) sum n coef_n u^{n-1} Fbar_n)
-//   M_m      = K^T Lambda_m   (K^T: same taps on zero-extended data, mirror images folded back)
+//   M_m      = K^T Lambda_m   (K^T: same taps on zero-extended data, mirror images folded back;
+//              k_plain.cu's row and column passes in adjoint mode)
 //   dL/df    = (D + sum_m M_m (m Fh_{m-1} - mu u Fh_m)) / s_r       (de/du = -mu u e)
 //   dL/dsigma_r = sum_i [ w s_r/Q sum_n coef'_n u^n (Fbar_{n+1} - (P/Q) Fbar_n) ]
 //               + sum_j [ sum_m M_m Fh_m ] (f - t_c)^2 / sigma_r^3,
@@ -80,47 +81,6 @@ __global__ void __launch_bounds__(256) k_adjoint_lambda(const float* __restrict_
 }
 
 // ---------------------------------------------------------------------------------------
-// Transposed 1-D Gaussian along one axis with the mirror extension folded back:
-//   out(j) = sum over images p of j in [-R, n-1+R] of sum_{i in [0,n), |p-i| <= R} g(p-i) x(i),
-// images of j: p = j + 2nk and p = -1 - j + 2nk.  Axis 0 = along x (rows), 1 = along y.
-template <int AXIS>
-__global__ void __launch_bounds__(256) k_adjoint_pass(const float* __restrict__ X, float* __restrict__ Y,
-                                                      const GcParams p, const Taps t, size_t cs) {
-    const int R = t.R, W = p.W, H = p.H;
-    const int n = AXIS == 0 ? W : H;
-    const size_t plane = (size_t)blockIdx.z * cs;
-    int x, y;
-    if (AXIS == 0) {
-        x = blockIdx.x * blockDim.x + threadIdx.x;
-        y = blockIdx.y;
-    } else {
-        x = blockIdx.x * 32 + (threadIdx.x & 31);
-        y = blockIdx.y * 8 + (threadIdx.x >> 5);
-    }
-    if (x >= W || y >= H) return;
-    const int j = AXIS == 0 ? x : y;
-    const size_t step = AXIS == 0 ? 1 : (size_t)W;
-    const float* line = X + plane + (AXIS == 0 ? (size_t)y * W : (size_t)x);
-    float acc = 0.0f;
-    // direct image p = j, then the others
-    for (int lo = j - R < 0 ? 0 : j - R, i = lo; i <= (j + R < n - 1 ? j + R : n - 1); ++i)
-        acc = fmaf(t.g[abs(j - i)], line[(size_t)i * step], acc);
-    if (j < R || j > n - 1 - R) {
-        const int period = 2 * n;
-        for (int k = -((R + n) / period) - 1; k <= (R + n) / period + 1; ++k) {
-            for (int s = 0; s < 2; ++s) {
-                const long pp = s == 0 ? (long)j + (long)period * k : -1L - j + (long)period * k;
-                if (pp == j || pp < -R || pp > n - 1 + R) continue;
-                const int ip = (int)pp;
-                const int lo = ip - R < 0 ? 0 : ip - R, hi = ip + R < n - 1 ? ip + R : n - 1;
-                for (int i = lo; i <= hi; ++i) acc = fmaf(t.g[abs(ip - i)], line[(size_t)i * step], acc);
-            }
-        }
-    }
-    Y[plane + (size_t)y * W + x] = acc;
-}
-
-// ---------------------------------------------------------------------------------------
 // dL/df and the per-block sums of the e-term of dL/dsigma_r.
 __global__ void __launch_bounds__(256) k_adjoint_assemble(const float* __restrict__ f, const float* __restrict__ Mch,
                                                           const float* __restrict__ Dterm, float* __restrict__ gf,
@@ -175,18 +135,6 @@ cudaError_t launch_adjoint_lambda(const float* f, const float* gout, const float
                                   double* partial, const GcParams& p, const AdjCoef& ac, size_t cs, cudaStream_t s) {
     const size_t px = (size_t)p.H * p.W;
     k_adjoint_lambda<<<kAdjBlocks, 256, 0, s>>>(f, gout, Z, Lam, Dterm, partial, p, ac, cs, px);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_adjoint_pass(int axis, const float* X, float* Y, const GcParams& p, const Taps& t, size_t cs,
-                                int planes, cudaStream_t s) {
-    if (axis == 0) {
-        dim3 grid((p.W + 255) / 256, p.H, planes);
-        k_adjoint_pass<0><<<grid, 256, 0, s>>>(X, Y, p, t, cs);
-    } else {
-        dim3 grid((p.W + 31) / 32, (p.H + 7) / 8, planes);
-        k_adjoint_pass<1><<<grid, 256, 0, s>>>(X, Y, p, t, cs);
-    }
     return cudaGetLastError();
 }
 

@@ -155,8 +155,11 @@ __global__ void __launch_bounds__(kPThreads, 1) k_vpass_combine_pairs(
                 const int it = k / CP, i = k - it * CP, s = k % S, use = k / S;
                 const int tile = (int)blockIdx.x + it * G;
                 const int x0 = (tile / tiles_y) * PC, y0 = (tile % tiles_y) * PR;
-                if (use > 0 && !mbar_wait_abort(&empty[s], (unsigned)((use - 1) & 1), abort_flag, diag, kPFlag))
+                if (use > 0 && !mbar_wait_abort(&empty[s], (unsigned)((use - 1) & 1), abort_flag, diag, kPFlag, p.wait_ns))
                     break;
+                // (test of the bounded waits, BF_OPT_STALL = 2: the first stage is never loaded;
+                // no copy is issued for it)
+                if (p.stall == 2 && k == 0) continue;
                 stage_k[s] = k;
                 mbar_expect_tx(&full[s], (unsigned)SP);
                 // padded rows y0 .. y0 + RIN of channels C-1-2i and C-2-2i (channel 0 again when
@@ -181,8 +184,8 @@ __global__ void __launch_bounds__(kPThreads, 1) k_vpass_combine_pairs(
                                    ((uint32_t)(PR >> 4) << 24);
             for (int k = 0; k < total; ++k) {
                 const int s = k % S, use = k / S, b = k % NB, buse = k / NB;
-                if (!mbar_wait_abort_poll(&full[s], (unsigned)(use & 1), abort_flag, diag, kPFlag)) break;
-                if (buse > 0 && !mbar_wait_abort_poll(&tempty[b], (unsigned)((buse - 1) & 1), abort_flag, diag, kPFlag))
+                if (!mbar_wait_abort_poll(&full[s], (unsigned)(use & 1), abort_flag, diag, kPFlag, p.wait_ns)) break;
+                if (buse > 0 && !mbar_wait_abort_poll(&tempty[b], (unsigned)((buse - 1) & 1), abort_flag, diag, kPFlag, p.wait_ns))
                     break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 // two 64-column MN blocks of B, SB bytes apart (the leading byte offset)
@@ -276,7 +279,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_vpass_combine_pairs(
             for (int i = 0; i < CP && ok; ++i, ++k) {
                 const int b = k % NB, m0 = C - 1 - 2 * i;
                 bool w = true;
-                if (lane == 0) w = mbar_wait_abort_poll(&tfull[b], (unsigned)((k / NB) & 1), abort_flag, diag, kPFlag);
+                if (lane == 0) w = mbar_wait_abort_poll(&tfull[b], (unsigned)((k / NB) & 1), abort_flag, diag, kPFlag, p.wait_ns);
                 ok = __shfl_sync(0xffffffffu, w, 0);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -291,26 +294,22 @@ __global__ void __launch_bounds__(kPThreads, 1) k_vpass_combine_pairs(
                 if (lane == 0) mbar_arrive(&tempty[b]);
                 if (m0 >= 1) horner(m0 - 1, z);
             }
-            // eq. (10): divided in FP32, guarded, or listed for the FP64 refinement (ratio_decision)
+            // eq. (10): divided in FP32, guarded, or listed for the FP64 refinement (ratio_decision).
+            // Every pixel is stored divided first; the few guarded or listed ones are rewritten
+            // with their input value afterwards (the loads of f stay off the common path).
             if (ok && y < p.H) {
                 float* orow = out + (size_t)y * p.W;
                 float o[16];
-                unsigned flagged = 0;
+                unsigned guard_m = 0, flag_m = 0;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int how = ratio_decision(p, u[j], P_[j], Q_[j], Qa[j]);
                     const bool in = xb + j < p.W;
-                    if (how >= 2) o[j] = in ? __ldg(f + (size_t)y * p.W + xb + j) : 0.0f;
-                    else o[j] = p.s_r * P_[j] / Q_[j] + p.t_c;
-                    guarded += in && how == 2;
+                    // 16-bit channels: a 2-ulp quotient (__fdividef) is far below their rounding
+                    o[j] = __fdividef(p.s_r * P_[j], Q_[j]) + p.t_c;
                     illcond += in && how == 1;
-                    flagged |= (unsigned)(in && how == 3) << j;
-                }
-                // pixels for the FP64 refinement (none where the fit converges)
-                if (__any_sync(__activemask(), flagged != 0)) {
-#pragma unroll 1
-                    for (int j = 0; j < 16; ++j)
-                        refine_push(p, diag, (flagged >> j) & 1u, (uint32_t)((size_t)y * p.W + xb + j));
+                    guard_m |= (unsigned)(in && how == 2) << j;
+                    flag_m |= (unsigned)(in && how == 3) << j;
                 }
                 if (vec && xb + 16 <= p.W) {
 #pragma unroll
@@ -320,6 +319,16 @@ __global__ void __launch_bounds__(kPThreads, 1) k_vpass_combine_pairs(
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
                         if (xb + j < p.W) orow[xb + j] = o[j];
+                }
+                // (none of either where the fit converges)
+                if (__any_sync(__activemask(), (guard_m | flag_m) != 0)) {
+                    guarded += __popc(guard_m);
+#pragma unroll 1
+                    for (int j = 0; j < 16; ++j)
+                        if (((guard_m | flag_m) >> j) & 1u) orow[xb + j] = __ldg(f + (size_t)y * p.W + xb + j);
+#pragma unroll 1
+                    for (int j = 0; j < 16; ++j)
+                        refine_push(p, diag, (flag_m >> j) & 1u, (uint32_t)((size_t)y * p.W + xb + j));
                 }
             }
         }

@@ -61,6 +61,30 @@ __host__ __device__ inline int hpass_pitch(int R) {
 }
 __host__ __device__ inline int taps_len(int R) { return (2 * R + 1 + 7) / 8 * 8; }
 
+// Adjoint of eq. (7) along one axis (the backward pass): with symmetric taps the transpose of
+// "mirror-extend, then filter" is "zero-extend, then filter" plus, for each output j within R
+// of an end, the contributions that the forward sent to the mirror images of j, folded back:
+//   sum over images p != j of j in [-R, n-1+R] of sum_{i in [0,n), |p-i| <= R} g(p-i) x(i),
+// images p = j + 2nk and p = -1 - j + 2nk.  Reads `line` (stride `step`) from global memory;
+// only outputs near the ends call it.
+__device__ float fold_back(const float* __restrict__ line, size_t step, int j, int n, const Taps& t) {
+    const int R = t.R, period = 2 * n;
+    float acc = 0.0f;
+    for (int k = -((R + n) / period) - 1; k <= (R + n) / period + 1; ++k) {
+        for (int sgn = 0; sgn < 2; ++sgn) {
+            const long pp = sgn == 0 ? (long)j + (long)period * k : -1L - j + (long)period * k;
+            if (pp == j || pp < -R || pp > n - 1 + R) continue;
+            const int ip = (int)pp;
+            const int lo = ip - R < 0 ? 0 : ip - R, hi = ip + R < n - 1 ? ip + R : n - 1;
+            for (int i = lo; i <= hi; ++i) acc = fmaf(t.g[abs(ip - i)], line[(size_t)i * step], acc);
+        }
+    }
+    return acc;
+}
+
+// ADJ = false: eq. (7) along x with mirror extension; ADJ = true: its adjoint (zero extension and
+// the mirror images folded back, see fold_back).
+template <bool ADJ>
 __global__ void __launch_bounds__(256) k_hpass(const float* __restrict__ X, float* __restrict__ Y,
                                                const GcParams p, const Taps t, size_t cs) {
     extern __shared__ __align__(16) float smem[];
@@ -84,7 +108,8 @@ __global__ void __launch_bounds__(256) k_hpass(const float* __restrict__ X, floa
                 const float* grow = src + (size_t)y * W;
                 for (int k = lane; k < LEN; k += 32) {
                     const int x = x0 - R + k;
-                    srow[k] = grow[(unsigned)x < (unsigned)W ? x : mirror(x, W)];
+                    if (ADJ) srow[k] = (unsigned)x < (unsigned)W ? grow[x] : 0.0f;
+                    else srow[k] = grow[(unsigned)x < (unsigned)W ? x : mirror(x, W)];
                 }
             } else {
                 for (int k = lane; k < LEN; k += 32) srow[k] = 0.0f;
@@ -129,18 +154,33 @@ __global__ void __launch_bounds__(256) k_hpass(const float* __restrict__ X, floa
     for (int idx = tid; idx < HP_ROWS * HP_COLS; idx += blockDim.x) {
         const int r = idx / HP_COLS, c = idx - r * HP_COLS;
         const int y = y0 + r, x = x0 + c;
-        if (y < H && x < W) dst[(size_t)y * W + x] = o[r * PITCH + c];
+        if (y < H && x < W) {
+            float v = o[r * PITCH + c];
+            if (ADJ && (x < R || x > W - 1 - R)) v += fold_back(src + (size_t)y * W, 1, x, W, t);
+            dst[(size_t)y * W + x] = v;
+        }
     }
+}
+
+template <bool ADJ>
+cudaError_t launch_hpass_t(const float* X, float* Y, const GcParams& p, const Taps& t, size_t cs, int planes,
+                           cudaStream_t s) {
+    const size_t smem = (size_t)(HP_ROWS * hpass_pitch(t.R) + taps_len(t.R)) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_hpass<ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((p.W + HP_COLS - 1) / HP_COLS, (p.H + HP_ROWS - 1) / HP_ROWS, planes);
+    k_hpass<ADJ><<<grid, 256, smem, s>>>(X, Y, p, t, cs);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_hpass(const float* X, float* Y, const GcParams& p, const Taps& t, size_t cs,
                          int planes, cudaStream_t s) {
-    const size_t smem = (size_t)(HP_ROWS * hpass_pitch(t.R) + taps_len(t.R)) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_hpass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((p.W + HP_COLS - 1) / HP_COLS, (p.H + HP_ROWS - 1) / HP_ROWS, planes);
-    k_hpass<<<grid, 256, smem, s>>>(X, Y, p, t, cs);
-    return cudaGetLastError();
+    return launch_hpass_t<false>(X, Y, p, t, cs, planes, s);
+}
+
+cudaError_t launch_hpass_adjoint(const float* X, float* Y, const GcParams& p, const Taps& t, size_t cs,
+                                 int planes, cudaStream_t s) {
+    return launch_hpass_t<true>(X, Y, p, t, cs, planes, s);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -150,6 +190,7 @@ constexpr int VP_ROWS = 64, VP_COLS = 64;
 
 __host__ __device__ inline int vpass_len(int R) { return VP_ROWS + 2 * R + 8; }
 
+template <bool ADJ>
 __global__ void __launch_bounds__(256) k_vpass(const float* __restrict__ X, float* __restrict__ Y,
                                                const GcParams p, const Taps t, size_t cs) {
     extern __shared__ __align__(16) float smem[];
@@ -167,7 +208,8 @@ __global__ void __launch_bounds__(256) k_vpass(const float* __restrict__ X, floa
         const int c = tid & (VP_COLS - 1), x = x0 + c;
         for (int r = tid / VP_COLS; r < LEN; r += 256 / VP_COLS) {
             const int y = y0 - R + r;
-            s[r * VP_COLS + c] = x < W ? src[(size_t)((unsigned)y < (unsigned)H ? y : mirror(y, H)) * W + x] : 0.0f;
+            if (ADJ) s[r * VP_COLS + c] = x < W && (unsigned)y < (unsigned)H ? src[(size_t)y * W + x] : 0.0f;
+            else s[r * VP_COLS + c] = x < W ? src[(size_t)((unsigned)y < (unsigned)H ? y : mirror(y, H)) * W + x] : 0.0f;
         }
     }
     __syncthreads();
@@ -197,19 +239,33 @@ __global__ void __launch_bounds__(256) k_vpass(const float* __restrict__ X, floa
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
             const int y = y0 + rb + v;
-            if (y < H && x < W) dst[(size_t)y * W + x] = acc[v];
+            if (y < H && x < W) {
+                if (ADJ && (y < R || y > H - 1 - R)) acc[v] += fold_back(src + x, (size_t)W, y, H, t);
+                dst[(size_t)y * W + x] = acc[v];
+            }
         }
     }
 }
 
-cudaError_t launch_vpass(const float* X, float* Y, const GcParams& p, const Taps& t, size_t cs,
-                         int planes, cudaStream_t s) {
+template <bool ADJ>
+cudaError_t launch_vpass_t(const float* X, float* Y, const GcParams& p, const Taps& t, size_t cs, int planes,
+                           cudaStream_t s) {
     const size_t smem = (size_t)(vpass_len(t.R) * VP_COLS + taps_len(t.R)) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_vpass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_vpass<ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((p.W + VP_COLS - 1) / VP_COLS, (p.H + VP_ROWS - 1) / VP_ROWS, planes);
-    k_vpass<<<grid, 256, smem, s>>>(X, Y, p, t, cs);
+    k_vpass<ADJ><<<grid, 256, smem, s>>>(X, Y, p, t, cs);
     return cudaGetLastError();
+}
+
+cudaError_t launch_vpass(const float* X, float* Y, const GcParams& p, const Taps& t, size_t cs,
+                         int planes, cudaStream_t s) {
+    return launch_vpass_t<false>(X, Y, p, t, cs, planes, s);
+}
+
+cudaError_t launch_vpass_adjoint(const float* X, float* Y, const GcParams& p, const Taps& t, size_t cs,
+                                 int planes, cudaStream_t s) {
+    return launch_vpass_t<true>(X, Y, p, t, cs, planes, s);
 }
 
 // ---------------------------------------------------------------------------------------

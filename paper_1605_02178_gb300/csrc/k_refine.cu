@@ -108,8 +108,10 @@ __global__ void __launch_bounds__(32 * kRefWarps) k_refine(const float* __restri
             float P, Q, Qa;
             window_sums<float, CH>(f, rp, rp.taps32, rp.coef32, rp.t_c32, rp.inv_sr32, rp.half_mu32, y, x, u0, lane,
                                    P, Q, Qa);
-            float tabs = rp.abs32;
-            if (fabsf(u0) > 1.0f) tabs *= __powf(fabsf(u0), (float)rp.N);
+            // the underflow allowance of ratio_decision, with A(|u|) = sum_n |coef_n| |u|^n
+            float A = 0.0f;
+            for (int n = rp.N; n >= 0; --n) A = fmaf(A, fabsf(u0), fabsf(rp.coef32[n]));
+            const float tabs = rp.abs32 * A;
             if (Qa > 0.0f && Qa <= 3.0e38f && fabsf(P) <= 3.0e38f && fabsf(Q) >= fmaf(rp.tier1_rel, Qa, tabs)) {
                 if (lane == 0) out[i] = rp.s_r32 * P / Q + rp.t_c32;
                 continue;

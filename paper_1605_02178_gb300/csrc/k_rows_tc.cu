@@ -46,7 +46,9 @@ namespace {
 
 constexpr int kRDrainWarps = 8;
 constexpr int kRGenWarps = 12;
-constexpr int kRThreads = 32 * (kRDrainWarps + kRGenWarps + 1);
+constexpr int kRMmaWarp = kRDrainWarps + kRGenWarps;          // warp 20: MMA issuer
+constexpr int kRStoreWarp = kRMmaWarp + 1;                     // warp 21: TMA stores of the tiles
+constexpr int kRThreads = 32 * (kRStoreWarp + 1);
 constexpr int kRGroupWarps = 4;                   // build groups of four warps (up to three)
 constexpr int kRGroups = kRGenWarps / kRGroupWarps;
 constexpr int kRGroupThreads = 32 * kRGroupWarps;
@@ -93,8 +95,8 @@ __device__ __forceinline__ void drain_sync() { asm volatile("bar.sync 1, %0;\n" 
 }  // namespace
 
 // Shared layout (1024-byte aligned): S stages of KB K-blocks | NS staging tiles | full[S] |
-// empty[S] | dfull[2] | dempty[2] | TMEM slot | abort flag | last tile committed per
-// accumulator buffer [2] | drain go flag | taps [kTapsSmem].
+// empty[S] | dfull[2] | dempty[2] | staged[2] | freed[2] | TMEM slot | abort flag | last tile
+// committed per accumulator buffer [2] | taps [kTapsSmem].
 template <typename T, int A_>
 __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_constant__ CUtensorMap ymap,
                                                                  const float* __restrict__ f, const GcParams p,
@@ -112,11 +114,12 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
     uint64_t* empty = full + S;
     uint64_t* dfull = empty + S;
     uint64_t* dempty = dfull + 2;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(dempty + 2);
+    uint64_t* staged = dempty + 2;                 // staging tile b holds a whole tile (8 drain warps)
+    uint64_t* freed = staged + 2;                  // its TMA store has read staging tile b
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(freed + 2);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     volatile int* last_d = abort_flag + 1;
-    volatile int* go = last_d + 2;
-    float* s_g = reinterpret_cast<float*>(smem + (size_t)S * SB + (size_t)NS * kRStgBytes + (2 * S + 4) * 8 + 32);
+    float* s_g = reinterpret_cast<float*>(smem + (size_t)S * SB + (size_t)NS * kRStgBytes + (2 * S + 8) * 8 + 32);
     const int tiles_x = (g.Wp + kRTile - 1) / kRTile, tiles_y = (g.Hp + TR - 1) / TR;
     const int ntiles = tiles_x * tiles_y, G = gridDim.x;
     const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;
@@ -165,7 +168,7 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
     if (is_build && grp < NG) load_f((int)blockIdx.x + grp * G);
 
     // ---- set-up: TMEM, barriers, row table, zero product rows M .. 127 of every stage
-    if (warp == kRDrainWarps + kRGenWarps) {
+    if (warp == kRMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" :: "r"(su32(tslot)), "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
@@ -177,6 +180,8 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
         for (int d = 0; d < 2; ++d) {
             mbar_init(&dfull[d], 1);
             mbar_init(&dempty[d], kRDrainWarps);
+            mbar_init(&staged[d], kRDrainWarps);
+            mbar_init(&freed[d], 1);
             last_d[d] = -1;
         }
         *abort_flag = 0;
@@ -221,7 +226,7 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
         // build tile `it` from `fv`, hand it to the MMA issuer, then fetch the group's next tile
         auto build = [&](int it) -> bool {
             const int s = it % S, use = it / S;
-            if (use > 0 && !mbar_wait_abort(&empty[s], (unsigned)((use - 1) & 1), abort_flag, diag, kRFlag))
+            if (use > 0 && !mbar_wait_abort(&empty[s], (unsigned)((use - 1) & 1), abort_flag, diag, kRFlag, p.wait_ns))
                 return false;
             unsigned char* B = stages + (size_t)s * SB;
             // channels e u^c of the fetched octets: 8 independent power chains per octet (packed
@@ -265,7 +270,9 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
             // one arrive per warp (256 arrives on one barrier would serialise on its word)
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(&full[s]);
+            // (test of the bounded waits, BF_OPT_STALL = 1: the first tile is never handed over;
+            // nothing asynchronous is outstanding for it)
+            if (lane == 0 && !(p.stall == 1 && it == 0)) mbar_arrive(&full[s]);
             load_f((int)blockIdx.x + (it + NG) * G);
             return true;
         };
@@ -275,7 +282,7 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
         if (grp < NG)
             for (int it = grp; it < my_tiles; it += NG)
                 if (!build(it)) break;
-    } else if (warp == kRDrainWarps + kRGenWarps) {
+    } else if (warp == kRMmaWarp) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             // D f32 (bit 4); A, B f16 (0) or bf16 (1) at bits 7, 10; both K-major (bits 15, 16
@@ -285,8 +292,8 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
                                    ((uint32_t)(kRTile >> 4) << 24);
             for (int it = 0; it < my_tiles; ++it) {
                 const int s = it % S, use = it / S, d = it & 1, duse = it >> 1;
-                if (!mbar_wait_abort(&full[s], (unsigned)(use & 1), abort_flag, diag, kRFlag)) break;
-                if (duse > 0 && !mbar_wait_abort(&dempty[d], (unsigned)((duse - 1) & 1), abort_flag, diag, kRFlag))
+                if (!mbar_wait_abort(&full[s], (unsigned)(use & 1), abort_flag, diag, kRFlag, p.wait_ns)) break;
+                if (duse > 0 && !mbar_wait_abort(&dempty[d], (unsigned)((duse - 1) & 1), abort_flag, diag, kRFlag, p.wait_ns))
                     break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint64_t b0 = sw128_desc(su32(stages + (size_t)s * SB));
@@ -309,6 +316,37 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
                              :: "r"(su32(&dfull[d])) : "memory");
             }
         }
+    } else if (warp == kRStoreWarp) {
+        // ------------------------------------------------------------ TMA stores
+        // for each tile: wait until the eight drain warps have staged it, store it (two boxes
+        // {64 columns, C channels, TR padded rows} from the two 128-byte-swizzled staging halves;
+        // rows past Hp and columns past Wp are clipped by the tensor map, a half that starts at or
+        // past Wp is skipped), then free the staging tile whose store has been read
+        if (lane == 0) {
+            for (int it = 0; it < my_tiles; ++it) {
+                const int b = it % NS;
+                if (!mbar_wait_abort(&staged[b], (unsigned)((it / NS) & 1), abort_flag, diag, kRFlag, p.wait_ns))
+                    break;
+                const int tile = (int)blockIdx.x + it * G;
+                const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+                unsigned char* sb = stg + (size_t)b * kRStgBytes;
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int xs = tx * kRTile + 64 * hh;
+                    if (xs >= g.Wp) break;
+                    asm volatile(
+                        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];\n"
+                        :: "l"(reinterpret_cast<uint64_t>(&ymap)), "r"(xs), "r"(0), "r"(ty * TR),
+                           "r"(su32(sb) + (uint32_t)hh * (kRStgBytes / 2))
+                        : "memory");
+                }
+                asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+                // the store of tile it - (NS - 1) has read its staging tile
+                if (NS > 1) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+                else asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+                mbar_arrive(&freed[(it - (NS - 1)) % NS]);
+            }
+            asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+        }
     } else {
         // ------------------------------------------------------------ drain
         const int q = warp & 3, h = warp >> 2;         // lane quarter, half of the product rows
@@ -318,18 +356,16 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
         // half x / 64 (64 columns, 128-byte rows, 128-byte swizzle: chunk j of row m at
         // j ^ (m & 7))
         const int mk = lane >> 3, mr = lane & 7;
+        // each warp on its own: wait for the accumulators (lane 0, bounded; the warp agrees)
+        auto wait_warp = [&](uint64_t* bar, unsigned parity) {
+            bool w = true;
+            if (lane == 0) w = mbar_wait_abort(bar, parity, abort_flag, diag, kRFlag, p.wait_ns);
+            return __shfl_sync(0xffffffffu, w, 0);
+        };
         for (int it = 0; it < my_tiles; ++it) {
-            const int d = it & 1, duse = it >> 1;
-            unsigned char* sb = stg + (size_t)(it % NS) * kRStgBytes;
-            // thread 0 waits for the accumulators and for the TMA store that last read this
-            // staging tile, then releases every drain warp (or stops all of them together)
-            if (tid == 0) {
-                if (NS > 1) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
-                else asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
-                *go = mbar_wait_abort(&dfull[d], (unsigned)(duse & 1), abort_flag, diag, kRFlag) ? 1 : 0;
-            }
-            drain_sync();
-            if (!*go) break;
+            const int d = it & 1, duse = it >> 1, b = it % NS;
+            unsigned char* sb = stg + (size_t)b * kRStgBytes;
+            if (!wait_warp(&dfull[d], (unsigned)(duse & 1))) break;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             // lanes 32q .. 32q + 15 (L = 0) and 32q + 16 .. 32q + 31 (L = 1), columns 64h .. 64h + 63
             uint32_t v0[32], v1[32];
@@ -339,6 +375,8 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&dempty[d]);
+            // the staging tile's previous store (tile it - NS) has read it
+            if (it >= NS && !wait_warp(&freed[b], (unsigned)((it / NS - 1) & 1))) break;
             // product rows m, m + 1 of one column x in one packed conversion; stmatrix with
             // transpose turns the fragments into 16-byte runs of 8 columns of one product row
             // (rows from M on are never stored)
@@ -359,27 +397,11 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
             };
             stage(v0, 0);
             stage(v1, 1);
+            // the writes reach the async proxy before the TMA store reads them
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            drain_sync();
-            if (tid == 0) {
-                const int tile = (int)blockIdx.x + it * G;
-                const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
-                // two boxes {64 columns, C channels, TR padded rows} at (x0 + 64 half, 0, p0), from
-                // the two 128-byte-swizzled staging halves; rows past Hp and columns past Wp are
-                // clipped by the tensor map, and a half that starts at or past Wp is skipped
-                for (int hh = 0; hh < 2; ++hh) {
-                    const int xs = tx * kRTile + 64 * hh;
-                    if (xs >= g.Wp) break;
-                    asm volatile(
-                        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];\n"
-                        :: "l"(reinterpret_cast<uint64_t>(&ymap)), "r"(xs), "r"(0), "r"(ty * TR),
-                           "r"(su32(sb) + (uint32_t)hh * (kRStgBytes / 2))
-                        : "memory");
-                }
-                asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
-            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&staged[b]);
         }
-        if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
     }
 
     // ---- drain: every MMA committed has completed (immediate unless a wait gave up), then
@@ -391,7 +413,7 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
             if (last_d[d] >= 0) mbar_wait_bounded(&dfull[d], (unsigned)((last_d[d] >> 1) & 1));
     }
     __syncthreads();
-    if (warp == kRDrainWarps + kRGenWarps) {
+    if (warp == kRMmaWarp) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tbase), "r"(512));
     }
@@ -404,7 +426,7 @@ size_t rows_tc_stage_bytes(int a) { return (size_t)((kRTile + 32 * a + 63) / 64)
 size_t rows_tc_stg_bytes() { return kRStgBytes; }
 
 size_t rows_tc_smem_bytes(const TcGeom& g) {
-    return (size_t)g.r_stages * rows_tc_stage_bytes(g.a) + (size_t)g.r_stg * kRStgBytes + (2 * g.r_stages + 4) * 8 +
+    return (size_t)g.r_stages * rows_tc_stage_bytes(g.a) + (size_t)g.r_stg * kRStgBytes + (2 * g.r_stages + 8) * 8 +
            32 + kTapsSmem * 4 + 1024;
 }
 

@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
                 const int it = k / C, i = k - it * C, s = stage_of(k), use = (k >> 1) / S2;
                 const int tile = (int)blockIdx.x + it * G;
                 const int x0 = (tile / tiles_y) * VC, y0 = (tile % tiles_y) * VR;
-                if (use > 0 && !mbar_wait_abort(&empty[s], (unsigned)((use - 1) & 1), abort_flag, diag, kVFlag))
+                if (use > 0 && !mbar_wait_abort(&empty[s], (unsigned)((use - 1) & 1), abort_flag, diag, kVFlag, p.wait_ns))
                     break;
                 stage_k[s] = k;
                 mbar_expect_tx(&full[s], (unsigned)SB);
@@ -193,8 +193,8 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
             for (int j = warp - kEpiWarps - 1; j < total; j += 2) {
                 const int s = stage_of(j), b = buf_of(j);
                 const int suse = (j >> 1) / S2, buse = (j >> 1) / NB2;
-                if (!mbar_wait_abort(&full[s], (unsigned)(suse & 1), abort_flag, diag, kVFlag)) break;
-                if (buse > 0 && !mbar_wait_abort(&tempty[b], (unsigned)((buse - 1) & 1), abort_flag, diag, kVFlag))
+                if (!mbar_wait_abort(&full[s], (unsigned)(suse & 1), abort_flag, diag, kVFlag, p.wait_ns)) break;
+                if (buse > 0 && !mbar_wait_abort(&tempty[b], (unsigned)((buse - 1) & 1), abort_flag, diag, kVFlag, p.wait_ns))
                     break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint64_t b0 = sw128_desc(su32(stages + (size_t)s * SB), SB);
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
             for (int i = 0; i < C && ok; ++i, ++gi) {
                 const int b = buf_of(gi), m = C - 1 - i;
                 bool w = true;
-                if (lane == 0) w = mbar_wait_abort_poll(&tfull[b], (unsigned)(((gi >> 1) / NB2) & 1), abort_flag, diag, kVFlag);
+                if (lane == 0) w = mbar_wait_abort_poll(&tfull[b], (unsigned)(((gi >> 1) / NB2) & 1), abort_flag, diag, kVFlag, p.wait_ns);
                 ok = __shfl_sync(0xffffffffu, w, 0);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -295,26 +295,22 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
                     }
                 }
             }
-            // eq. (10): divided in FP32, guarded, or listed for the FP64 refinement (ratio_decision)
+            // eq. (10): divided in FP32, guarded, or listed for the FP64 refinement (ratio_decision).
+            // Every pixel is stored divided first; the few guarded or listed ones are rewritten
+            // with their input value afterwards (the loads of f stay off the common path).
             if (ok && y < p.H) {
                 float* orow = out + (size_t)y * p.W;
                 float o[16];
-                unsigned flagged = 0;
+                unsigned guard_m = 0, flag_m = 0;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int how = ratio_decision(p, u[j], P_[j], Q_[j], Qa[j]);
                     const bool in = xb + j < p.W;
-                    if (how >= 2) o[j] = in ? __ldg(f + (size_t)y * p.W + xb + j) : 0.0f;
-                    else o[j] = p.s_r * P_[j] / Q_[j] + p.t_c;
-                    guarded += in && how == 2;
+                    // 16-bit channels: a 2-ulp quotient (__fdividef) is far below their rounding
+                    o[j] = __fdividef(p.s_r * P_[j], Q_[j]) + p.t_c;
                     illcond += in && how == 1;
-                    flagged |= (unsigned)(in && how == 3) << j;
-                }
-                // pixels for the FP64 refinement (none where the fit converges)
-                if (__any_sync(__activemask(), flagged != 0)) {
-#pragma unroll 1
-                    for (int j = 0; j < 16; ++j)
-                        refine_push(p, diag, (flagged >> j) & 1u, (uint32_t)((size_t)y * p.W + xb + j));
+                    guard_m |= (unsigned)(in && how == 2) << j;
+                    flag_m |= (unsigned)(in && how == 3) << j;
                 }
                 if (vec && xb + 16 <= p.W) {
 #pragma unroll
@@ -324,6 +320,16 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
                         if (xb + j < p.W) orow[xb + j] = o[j];
+                }
+                // (none of either where the fit converges)
+                if (__any_sync(__activemask(), (guard_m | flag_m) != 0)) {
+                    guarded += __popc(guard_m);
+#pragma unroll 1
+                    for (int j = 0; j < 16; ++j)
+                        if (((guard_m | flag_m) >> j) & 1u) orow[xb + j] = __ldg(f + (size_t)y * p.W + xb + j);
+#pragma unroll 1
+                    for (int j = 0; j < 16; ++j)
+                        refine_push(p, diag, (flag_m >> j) & 1u, (uint32_t)((size_t)y * p.W + xb + j));
                 }
             }
         }

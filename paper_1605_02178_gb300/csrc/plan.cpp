@@ -125,7 +125,10 @@ void refit(bf_gc_plan_s* p) {
     g.refine = nullptr;
     g.flag_rel = kFlagRelFp32;
     g.flag_abs = 0.0f;
+    g.flag_abs_sum = 0.0f;
     g.guard_rel = kGuardRel32;
+    g.wait_ns = (unsigned long long)(p->wait_us * 1000.0);
+    g.stall = p->stall;
 
     RefineParams& r = p->rp;
     r.H = p->H; r.W = p->W; r.N = p->N; r.C = p->C; r.R = p->R;
@@ -139,12 +142,8 @@ void refit(bf_gc_plan_s* p) {
     r.s_r32 = g.s_r;
     r.half_mu32 = g.half_mu;
     r.tier1_rel = kTier1Rel;
-    double a1 = 0.0;
-    for (int n = 0; n < BF_MAX_C; ++n) {
-        r.coef32[n] = g.coef[n];
-        a1 += fabs((double)g.coef[n]);
-    }
-    r.abs32 = (float)(kFlagAbsFp32 * a1);
+    for (int n = 0; n < BF_MAX_C; ++n) r.coef32[n] = g.coef[n];
+    r.abs32 = kFlagAbsFp32;
     r.tier1 = 0;                                   // set per call from the storage precision
 }
 
@@ -302,6 +301,7 @@ bf_status bf_gc_plan(int H, int W, double sigma_s, double sigma_r, int N, bf_gc_
     p->L = 0.0; p->U = 255.0;
     p->form = BF_FORM_PLAIN; p->precision = BF_PREC_FP32; p->poly = BF_POLY_CHEBYSHEV; p->form_auto = false;
     p->save_channels = 0; p->tile_w = 0; p->refine = 1; p->used = false;
+    p->wait_us = 1e6; p->stall = 0;
     refit(p);
     make_taps(sigma_s, R, &p->taps, p->rp.taps, p->rp.taps32);
     *out = p;
@@ -344,6 +344,16 @@ bf_status bf_gc_plan_set(bf_gc_plan_t p, int option, double value) {
     case BF_OPT_REFINE:
         if (iv != value || (iv != 0 && iv != 1)) return BF_ERR_INVALID_ARG;
         p->refine = iv;
+        return BF_OK;
+    case BF_OPT_WAIT_US:
+        if (!(value >= 1.0 && value <= 1e7)) return BF_ERR_INVALID_ARG;
+        p->wait_us = value;
+        p->gp.wait_ns = (unsigned long long)(value * 1000.0);
+        return BF_OK;
+    case BF_OPT_STALL:
+        if (iv != value || iv < 0 || iv > 2) return BF_ERR_INVALID_ARG;
+        p->stall = iv;
+        p->gp.stall = iv;
         return BF_OK;
     case BF_OPT_TILE_W:
         if (iv != value || (iv != 0 && iv != 64 && iv != 128 && iv != 256)) return BF_ERR_INVALID_ARG;
@@ -401,7 +411,8 @@ bf_status bf_gc_forward(bf_gc_plan_t p, const float* f, float* out, void* ws, si
                                                      : kFlagRelFp32;
         double a1 = 0.0;                                   // sum_n |coef_n|
         for (int n = 0; n <= p->N; ++n) a1 += fabs((double)gp.coef[n]);
-        gp.flag_abs = (float)((p->precision == BF_PREC_FP16 ? kFlagAbsFp16 : kFlagAbsFp32) * a1);
+        gp.flag_abs = p->precision == BF_PREC_FP16 ? kFlagAbsFp16 : kFlagAbsFp32;
+        gp.flag_abs_sum = (float)(gp.flag_abs * a1);
     }
     switch (p->form) {
     case BF_FORM_PLAIN: {
@@ -502,19 +513,25 @@ bf_status bf_gc_backward(bf_gc_plan_t p, const float* f, const float* gout, floa
     cudaError_t e = cudaSuccess;
     do {
         if (!(p->save_channels && p->form == BF_FORM_PLAIN)) {      // filtered channels -> X
-            prof_mark(p, "build", s);
-            if ((e = bfgc::launch_build(f, X, p->gp, cs, s)) != cudaSuccess) break;
-            prof_mark(p, "hpass", s);
-            if ((e = bfgc::launch_hpass(X, Y, p->gp, p->taps, cs, p->C, s)) != cudaSuccess) break;
+            if (bfgc::fused_f32_supported(p->R)) {
+                // channels and row pass in one kernel (the plain form's operations, same bits)
+                prof_mark(p, "build_hpass_f32", s);
+                if ((e = bfgc::launch_build_hpass_f32(f, Y, p->gp, p->taps, cs, s)) != cudaSuccess) break;
+            } else {
+                prof_mark(p, "build", s);
+                if ((e = bfgc::launch_build(f, X, p->gp, cs, s)) != cudaSuccess) break;
+                prof_mark(p, "hpass", s);
+                if ((e = bfgc::launch_hpass(X, Y, p->gp, p->taps, cs, p->C, s)) != cudaSuccess) break;
+            }
             prof_mark(p, "vpass", s);
             if ((e = bfgc::launch_vpass(Y, X, p->gp, p->taps, cs, p->C, s)) != cudaSuccess) break;
         }
         prof_mark(p, "adjoint_lambda", s);
         if ((e = bfgc::launch_adjoint_lambda(f, gout, X, Y, Dt, partial, p->gp, ac, cs, s)) != cudaSuccess) break;
         prof_mark(p, "adjoint_vpass", s);       // K = V H, so K^T = H^T V^T
-        if ((e = bfgc::launch_adjoint_pass(1, Y, X, p->gp, p->taps, cs, p->C, s)) != cudaSuccess) break;
+        if ((e = bfgc::launch_vpass_adjoint(Y, X, p->gp, p->taps, cs, p->C, s)) != cudaSuccess) break;
         prof_mark(p, "adjoint_hpass", s);
-        if ((e = bfgc::launch_adjoint_pass(0, X, Y, p->gp, p->taps, cs, p->C, s)) != cudaSuccess) break;
+        if ((e = bfgc::launch_hpass_adjoint(X, Y, p->gp, p->taps, cs, p->C, s)) != cudaSuccess) break;
         prof_mark(p, "adjoint_assemble", s);
         if ((e = bfgc::launch_adjoint_assemble(f, Y, Dt, gf, partial + bfgc::kAdjBlocks, p->gp, ac, cs, s)) !=
             cudaSuccess)

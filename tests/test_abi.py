@@ -171,3 +171,23 @@ def test_bench_roofline_model_names_the_profiled_kernels():
         assert marks and marks == set(bench.kernel_model(form, prec, 22, 30)), form
         seen.add(form)
     assert seen == set(forms.values())
+
+
+def test_wait_stall_and_refine_options_are_checked():
+    p = B.bf_gc_plan(64, 64, 2.0, 50.0, 8)
+    try:
+        for opt, bad in ((B.BF_OPT_WAIT_US, 0.5), (B.BF_OPT_WAIT_US, 2e7), (B.BF_OPT_STALL, 3),
+                         (B.BF_OPT_STALL, 1.5), (B.BF_OPT_REFINE, 2), (B.BF_OPT_REFINE, -1)):
+            with pytest.raises(B.BfError) as e:
+                B.bf_gc_plan_set(p, opt, bad)
+            assert e.value.status == B.BF_ERR_INVALID_ARG
+        for opt, good in ((B.BF_OPT_WAIT_US, 2000.0), (B.BF_OPT_STALL, 2), (B.BF_OPT_STALL, 0),
+                          (B.BF_OPT_REFINE, 0)):
+            B.bf_gc_plan_set(p, opt, good)
+        # without the refinement the forward workspace holds no list
+        B.bf_gc_plan_set(p, B.BF_OPT_REFINE, 1)
+        with_list = B.bf_gc_workspace_size(p)[0]
+        B.bf_gc_plan_set(p, B.BF_OPT_REFINE, 0)
+        assert B.bf_gc_workspace_size(p)[0] == with_list - 64 * 64 * 4
+    finally:
+        B.bf_gc_plan_destroy(p)

@@ -36,6 +36,7 @@ CASES = [
     (7, 9, 4.0, 50.0, 12),        # repeated reflection on both axes
     (1, 30, 2.0, 50.0, 8),
     (96, 80, 5.0, 50.0, 20),
+    (150, 530, 8.0, 50.0, 12),    # several row and column blocks, fold-back at all four edges
 ]
 
 
@@ -119,3 +120,29 @@ def test_grad1024_crop_against_oracle_and_finite_differences():
         fm[2 * R, 2 * R] -= h
         fd = (loss(fp) - loss(fm)) / (2 * h)
         assert gref[yy, xx] == pytest.approx(fd, rel=1e-5, abs=1e-9)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_autograd_function_with_saved_channels(dtype):
+    """GCBilateral on a save_channels plan: the backward reuses the channels of its own forward
+    (a workspace kept per call), giving the recomputing plan's gradients bit for bit; dL/dsigma_r
+    comes back in sigma_r's dtype and shape; a sigma_r other than the plan's is refused."""
+    H, W, ss, sr, N = 70, 90, 3.0, 50.0, 12
+    f = torch.from_numpy(synth.rects_image(H, W, seed=3)).cuda()
+    w = torch.from_numpy(synth.weight_map(H, W, seed=4)).cuda()
+    grads = []
+    for save in (False, True):
+        plan = api.GCPlan(H, W, ss, sr, N, save_channels=save)
+        x = f.clone().requires_grad_(True)
+        s_r = torch.tensor(sr, dtype=dtype, device="cuda", requires_grad=True)
+        other = torch.from_numpy(synth.rects_image(H, W, seed=5)).cuda()
+        out = api.GCBilateral.apply(x, s_r, plan)
+        plan.forward(other)                       # another image through the same plan in between
+        (out * w).sum().backward()
+        torch.cuda.synchronize()
+        assert s_r.grad.dtype == dtype and s_r.grad.shape == s_r.shape
+        grads.append((x.grad.clone(), float(s_r.grad)))
+    assert torch.equal(grads[0][0], grads[1][0]) and grads[0][1] == grads[1][1]
+    with pytest.raises(ValueError):
+        api.GCBilateral.apply(f.clone().requires_grad_(True), torch.tensor(sr + 1.0, device="cuda"),
+                              api.GCPlan(H, W, ss, sr, N))
