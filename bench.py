@@ -279,10 +279,11 @@ def run_ours(args):
     clocks_path = os.path.join("/tmp", f"bfgc_clocks_{os.getpid()}.csv")
     for key in plans:
         is_head = key == headline
-        ms, kern, clocks = time_form(key, args.steps, max(args.warmup, 3), profile=is_head,
-                                     clocks_path=clocks_path if is_head else None)
-        if not is_head:                      # per-kernel times of the other forms: a short profiled run
-            kern = time_form(key, 3, 1, profile=True)[1]
+        # the timed run records events only around the whole region; the per-kernel split comes
+        # from a separate profiled run (events between kernels would add gaps to the timed steps)
+        ms, _, clocks = time_form(key, args.steps, max(args.warmup, 3), profile=False,
+                                  clocks_path=clocks_path if is_head else None)
+        kern = time_form(key, args.steps if is_head else 3, 1, profile=True)[1]
         results[key] = {"ms": ms, "kernels": kern, "clocks": clocks,
                         "value": world * px / (ms * 1e-3) / 1e6}
 

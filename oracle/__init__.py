@@ -6,9 +6,7 @@ and shares no code with it.
 
 The arithmetic lives in ``bfgc_oracle.c`` (plain C, double precision); this
 module only marshals numpy arrays to it.  ``grad_ref`` holds the gradient
-oracle (plain PyTorch CPU float64 autograd over the same algorithm);
-``sweep_psnr`` is a study run by hand (the approximation's accuracy over a
-parameter sweep, from this package alone).
+oracle (plain PyTorch CPU float64 autograd over the same algorithm).
 
 Paper sections followed (see the C file for the per-function citations):
   eq. (1)            exact bilateral filter           -> exact_bf, exact_bf_at
