@@ -35,6 +35,14 @@ __device__ __forceinline__ int ratio_decision(const GcParams& p, float u, float 
     return lhs < (float)kIllcondRel * Qa ? 1 : 0;
 }
 
+// The common case of ratio_decision, cheaply: true only where ratio_decision is 0 (a finite,
+// conditioned pixel in [L, U]); the rest take ratio_decision itself.
+__device__ __forceinline__ bool ratio_clear(const GcParams& p, float u, float P, float Q, float Qa) {
+    const float au = fabsf(u);
+    return au <= 1.0f && Qa > 0.0f && Qa <= 3.0e38f && fabsf(P) <= 3.0e38f &&
+           fabsf(Q) >= fmaf(p.clear_rel, Qa, fmaf(au, p.flag_abs_sum, p.flag_abs0));
+}
+
 // Per-pixel accumulation of eqs. (8)-(9) by Horner's rule in u = (f - t_c)/s_r over the
 // filtered channels Z_m, visited from m = N+1 down to 0:
 //   P = sum_{n=0}^{N} coef_n u^n Z_{n+1},  Q = sum_{n=0}^{N} coef_n u^n Z_n,

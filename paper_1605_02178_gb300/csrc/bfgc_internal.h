@@ -49,6 +49,10 @@ struct GcParams {
     int H, W, N, C, R;
     float t_c, inv_sr, s_r, half_mu;
     float flag_rel, flag_abs, flag_abs_sum, guard_rel;
+    // ratio_clear: ratio_decision is 0 (divide, nothing to count) when |u| <= 1, the sums are
+    // finite and |Q| >= clear_rel Qa + flag_abs0 + |u| flag_abs_sum (clear_rel = flag_rel with the
+    // refinement, 1e-3 without; flag_abs0 = flag_abs |coef_0|)
+    float clear_rel, flag_abs0;
     uint32_t* refine;
     // bound of one pipeline wait in the tensor-core kernels (BF_OPT_WAIT_US), and the test-only
     // stall of BF_OPT_STALL (0: none; 1: the row pass's first build group withholds its first

@@ -43,6 +43,11 @@ int rows_tc_max_octets();
 size_t rows_tc_stage_bytes(int a);
 size_t rows_tc_stg_bytes();
 size_t rows_tc_smem_bytes(const TcGeom& g);
+// The driver's cuTensorMapEncodeTiled, looked up once (null if unavailable)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_fn();
 // Tensor map of the row-filtered buffer Y[p][c][x] (3-D: x, c, p) with the given box
 cudaError_t encode_y_map(CUtensorMap* map, void* Y, const TcGeom& g, int C, bool fp16, int box_x, int box_c,
                          int box_rows, bool swizzle128);

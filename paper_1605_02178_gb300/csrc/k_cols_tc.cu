@@ -25,8 +25,10 @@
 //   warps 0 .. 15     : ratio epilogue, one thread per output row and 16 columns: per pair two
 //                       tcgen05.ld of 16 accumulators, each followed by the Horner step of P, Q
 //                       and the guard scale for its channel (highest channel first); at the end of
-//                       a tile the guarded ratio and the un-centring.  The next tile's input
-//                       pixels are staged in shared memory by coalesced cp.async meanwhile.
+//                       a tile the ratio and the un-centring into an output tile in shared memory.
+// The tile's input pixels arrive by TMA with its first channel pair (the producer loads them once
+// every epilogue warp has read the previous tile's), and one thread stores the output tile by
+// TMA, so the epilogue issues no global loads or stores on the common path.
 // With C odd the last pair of a tile repeats channel 0 in its second half, which the epilogue
 // ignores.  Every mbarrier wait is bounded; a wait that runs out flags the workspace and raises
 // a shared abort flag that ends the other roles' waits, so the kernel always returns.
@@ -50,8 +52,14 @@ constexpr int PC = 64;                           // output columns per tile and 
 constexpr int kPEpiWarps = 16;                   // 4 per tensor-memory lane quarter
 constexpr int kPThreads = 32 * (kPEpiWarps + 2);
 constexpr unsigned kPFlag = 8u;                  // error flag of this kernel's waits
-constexpr int kPFPitch = PC + 4;                 // floats per row of the staged input tile
-constexpr int kPFBytes = PR * kPFPitch * 4;
+// The tile's input pixels and output values pass through shared memory as two boxes {32
+// columns, 128 rows} of FP32 each (128-byte swizzle: 16-byte chunk c of row r at c ^ (r & 7)),
+// loaded and stored by TMA: kPIoBytes for the input tile, as much for the output tile.
+constexpr int kPIoBytes = PR * PC * 4;
+constexpr int kPIoHalf = kPIoBytes / 2;
+// Dynamic shared memory a CTA may use: the 227 KB opt-in limit less the static taps array
+// (kTapsSmem floats).
+constexpr size_t kPSmemLimit = 227 * 1024 - 4 * 132;
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int c, int y, uint64_t* bar) {
     asm volatile(
@@ -59,9 +67,20 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         :: "r"(su32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(c), "r"(y), "r"(su32(bar))
         : "memory");
 }
-
-__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" :: "r"(su32(dst)), "l"(src) : "memory");
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+        :: "r"(su32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];\n"
+                 :: "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(src)) : "memory");
+}
+// Byte offset of the 16-byte chunk holding columns 4c .. 4c + 3 (c = 0 .. 15) of row r in an
+// input or output tile (two 128-byte-swizzled halves of 32 columns)
+__device__ __forceinline__ uint32_t io_chunk(int r, int c) {
+    return (uint32_t)((c >> 3) * kPIoHalf + r * 128 + (((c & 7) ^ (r & 7)) << 4));
 }
 
 }  // namespace
@@ -70,13 +89,15 @@ __host__ __device__ inline int vp_rows_in(int a) { return PR + 32 * a; }
 __host__ __device__ inline int vp_a_cols(int a) { return vp_rows_in(a) / 2; }
 __host__ __device__ inline int vp_bufs(int a) { return (512 - vp_a_cols(a)) / 128; }
 
-// Shared layout (1024-byte aligned): S stages of two channel blocks | f tile [128][68] |
-// full[S] | empty[S] | tfull[NB] | tempty[NB] | TMEM slot | abort flag | last step loaded per
-// stage [S] | last step committed per accumulator buffer [NB].  Pair step k uses stage k mod S
-// and accumulator buffer k mod NB.
+// Shared layout (1024-byte aligned): S stages of two channel blocks | input tile | output tile |
+// full[S] | empty[S] | tfull[NB] | tempty[NB] | ffull | ffree | TMEM slot | abort flag | last step
+// loaded per stage [S] | last step committed per accumulator buffer [NB] | last input tile
+// loaded.  Pair step k uses stage k mod S and accumulator buffer k mod NB.  Needs W % 4 == 0 (the
+// row pitch of f and out is a TMA stride).
 template <typename T, int A_>
 __global__ void __launch_bounds__(kPThreads, 1) k_vpass_combine_pairs(
-    const __grid_constant__ CUtensorMap ymap, const float* __restrict__ f, float* __restrict__ out, const GcParams p,
+    const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUtensorMap fmap,
+    const __grid_constant__ CUtensorMap omap, const float* __restrict__ f, float* __restrict__ out, const GcParams p,
     const Taps t, TcGeom g, DiagHeader* diag) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
@@ -87,15 +108,19 @@ __global__ void __launch_bounds__(kPThreads, 1) k_vpass_combine_pairs(
     const int S = g.vp_stages, C = p.C, P = g.P, CP = (C + 1) / 2;
     const int box_rows = g.kb_box_rows, loads = RIN / box_rows;
     unsigned char* stages = smem;
-    float* fs = reinterpret_cast<float*>(smem + (size_t)S * SP);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * SP + kPFBytes);
+    unsigned char* fs = smem + (size_t)S * SP;                 // input tile (TMA load)
+    unsigned char* os = fs + kPIoBytes;                        // output tile (TMA store)
+    uint64_t* full = reinterpret_cast<uint64_t*>(os + kPIoBytes);
     uint64_t* empty = full + S;
     uint64_t* tfull = empty + S;
     uint64_t* tempty = tfull + NB;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(tempty + NB);
+    uint64_t* ffull = tempty + NB;                             // the input tile has landed
+    uint64_t* ffree = ffull + 1;                               // every epilogue warp has read it
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(ffree + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     volatile int* stage_k = abort_flag + 1;
     volatile int* buf_j = stage_k + S;
+    volatile int* f_last = buf_j + NB;
     const int tiles_y = (g.Hp - 2 * P) / PR, tiles_x = g.Wp / PC;
     const int ntiles = tiles_x * tiles_y, G = gridDim.x;
     const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;
@@ -119,6 +144,9 @@ __global__ void __launch_bounds__(kPThreads, 1) k_vpass_combine_pairs(
             mbar_init(&tempty[b], kPEpiWarps);
             buf_j[b] = -1;
         }
+        mbar_init(ffull, 1);
+        mbar_init(ffree, kPEpiWarps);
+        *f_last = -1;
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -155,6 +183,16 @@ __global__ void __launch_bounds__(kPThreads, 1) k_vpass_combine_pairs(
                 const int it = k / CP, i = k - it * CP, s = k % S, use = k / S;
                 const int tile = (int)blockIdx.x + it * G;
                 const int x0 = (tile / tiles_y) * PC, y0 = (tile % tiles_y) * PR;
+                if (i == 0) {
+                    // the tile's input pixels, two boxes {32 columns, 128 rows} of f (zero outside
+                    // the image), once every epilogue warp has read the previous tile's
+                    if (it > 0 && !mbar_wait_abort(ffree, (unsigned)((it - 1) & 1), abort_flag, diag, kPFlag, p.wait_ns))
+                        break;
+                    *f_last = it;
+                    mbar_expect_tx(ffull, (unsigned)kPIoBytes);
+                    tma_load_2d(fs, &fmap, x0, y0, ffull);
+                    tma_load_2d(fs + kPIoHalf, &fmap, x0 + 32, y0, ffull);
+                }
                 if (use > 0 && !mbar_wait_abort(&empty[s], (unsigned)((use - 1) & 1), abort_flag, diag, kPFlag, p.wait_ns))
                     break;
                 // (test of the bounded waits, BF_OPT_STALL = 2: the first stage is never loaded;
@@ -212,48 +250,32 @@ __global__ void __launch_bounds__(kPThreads, 1) k_vpass_combine_pairs(
         const int q = warp & 3, cg = warp >> 2;
         const int row = 32 * q + lane;                     // tile-local output row = TMEM lane
         const uint32_t tl = tacc + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * cg);
-        const bool vec = (p.W & 3) == 0;
+        const uint32_t fsa = su32(fs), osa = su32(os);
         unsigned guarded = 0, illcond = 0;
         bool ok = true;
-        // the tile's 128 x 64 input pixels into fs, 16 bytes per copy, consecutive threads on
-        // consecutive addresses (t_c outside the image)
-        auto fetch_f = [&](int tile) {
-            if (tile >= ntiles) return;
-            const int y0 = (tile % tiles_y) * PR, x0 = (tile / tiles_y) * PC;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int c = tid + 512 * k, r = c >> 4, x = x0 + 4 * (c & 15), y = y0 + r;
-                float* dst = fs + r * kPFPitch + 4 * (c & 15);
-                const float* src = f + (size_t)y * p.W + x;
-                if (vec && y < p.H && x + 4 <= p.W) {
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" :: "r"(su32(dst)), "l"(src) : "memory");
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        if (y < p.H && x + e < p.W) cp_async4(dst + e, src + e);
-                        else dst[e] = p.t_c;
-                    }
-                }
-            }
-            asm volatile("cp.async.commit_group;\n" ::: "memory");
-        };
         auto epi_sync = [] { asm volatile("bar.sync 1, 512;\n" ::: "memory"); };
-        fetch_f(blockIdx.x);
         int k = 0;
         for (int it = 0; it < my_tiles; ++it) {
             const int tile = (int)blockIdx.x + it * G;
-            const int y = (tile % tiles_y) * PR + row, xb = (tile / tiles_y) * PC + 16 * cg;
+            const int x0 = (tile / tiles_y) * PC, y0 = (tile % tiles_y) * PR;
+            const int y = y0 + row, xb = x0 + 16 * cg;
             float u[16], P_[16], Q_[16], Qa[16];
-            // this tile's pixels (every warp passes both barriers, also after an abort)
-            asm volatile("cp.async.wait_all;\n" ::: "memory");
-            epi_sync();
+            // this tile's input pixels (TMA): this thread's 16, then the tile is released
+            if (ok) {
+                bool w = true;
+                if (lane == 0) w = mbar_wait_abort(ffull, (unsigned)(it & 1), abort_flag, diag, kPFlag, p.wait_ns);
+                ok = __shfl_sync(0xffffffffu, w, 0);
+            }
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const float4 v = *reinterpret_cast<const float4*>(fs + row * kPFPitch + 16 * cg + 4 * e);
+                float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (ok)
+                    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+                                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(fsa + io_chunk(row, 4 * cg + e)));
                 u[4 * e] = v.x; u[4 * e + 1] = v.y; u[4 * e + 2] = v.z; u[4 * e + 3] = v.w;
             }
-            epi_sync();
-            fetch_f(tile + G);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(ffree);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 u[j] = (u[j] - p.t_c) * p.inv_sr;
@@ -294,45 +316,63 @@ __global__ void __launch_bounds__(kPThreads, 1) k_vpass_combine_pairs(
                 if (lane == 0) mbar_arrive(&tempty[b]);
                 if (m0 >= 1) horner(m0 - 1, z);
             }
-            // eq. (10): divided in FP32, guarded, or listed for the FP64 refinement (ratio_decision).
-            // Every pixel is stored divided first; the few guarded or listed ones are rewritten
-            // with their input value afterwards (the loads of f stay off the common path).
-            if (ok && y < p.H) {
-                float* orow = out + (size_t)y * p.W;
-                float o[16];
-                unsigned guard_m = 0, flag_m = 0;
+            // eq. (10) into the output tile, which one thread then stores (TMA; clipped to the
+            // image).  The tile is free once the previous tile's store has read it.  Pixels the
+            // cheap test (ratio_clear) does not clear take the full decision (ratio_decision);
+            // guarded or listed ones hold their input value (none of either where the fit
+            // converges; the loads of f stay off this path).
+            if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+            epi_sync();
+            if (ok) {
+                unsigned odd = 0;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int how = ratio_decision(p, u[j], P_[j], Q_[j], Qa[j]);
-                    const bool in = xb + j < p.W;
-                    // 16-bit channels: a 2-ulp quotient (__fdividef) is far below their rounding
-                    o[j] = __fdividef(p.s_r * P_[j], Q_[j]) + p.t_c;
-                    illcond += in && how == 1;
-                    guard_m |= (unsigned)(in && how == 2) << j;
-                    flag_m |= (unsigned)(in && how == 3) << j;
+                for (int e = 0; e < 4; ++e) {
+                    float o[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        const int j = 4 * e + h;
+                        // 16-bit channels: a 2-ulp quotient (__fdividef) is far below their rounding
+                        o[h] = __fdividef(p.s_r * P_[j], Q_[j]) + p.t_c;
+                        odd |= (unsigned)(y < p.H && xb + j < p.W && !ratio_clear(p, u[j], P_[j], Q_[j], Qa[j])) << j;
+                    }
+                    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n"
+                                 :: "r"(osa + io_chunk(row, 4 * cg + e)), "f"(o[0]), "f"(o[1]), "f"(o[2]), "f"(o[3])
+                                 : "memory");
                 }
-                if (vec && xb + 16 <= p.W) {
+                if (__any_sync(0xffffffffu, odd != 0)) {
+                    unsigned redo = 0, flag_m = 0;
 #pragma unroll
-                    for (int j = 0; j < 16; j += 4)
-                        *reinterpret_cast<float4*>(orow + xb + j) = make_float4(o[j], o[j + 1], o[j + 2], o[j + 3]);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (xb + j < p.W) orow[xb + j] = o[j];
-                }
-                // (none of either where the fit converges)
-                if (__any_sync(__activemask(), (guard_m | flag_m) != 0)) {
-                    guarded += __popc(guard_m);
+                    for (int j = 0; j < 16; ++j) {
+                        if ((odd >> j) & 1u) {
+                            const int how = ratio_decision(p, u[j], P_[j], Q_[j], Qa[j]);
+                            illcond += how == 1;
+                            guarded += how == 2;
+                            redo |= (unsigned)(how >= 2) << j;
+                            flag_m |= (unsigned)(how == 3) << j;
+                        }
+                    }
 #pragma unroll 1
-                    for (int j = 0; j < 16; ++j)
-                        if (((guard_m | flag_m) >> j) & 1u) orow[xb + j] = __ldg(f + (size_t)y * p.W + xb + j);
-#pragma unroll 1
-                    for (int j = 0; j < 16; ++j)
-                        refine_push(p, diag, (flag_m >> j) & 1u, (uint32_t)((size_t)y * p.W + xb + j));
+                    for (int j = 0; j < 16; ++j) {
+                        const size_t i = (size_t)y * p.W + xb + j;
+                        if ((redo >> j) & 1u) {
+                            const uint32_t a = osa + io_chunk(row, (16 * cg + j) >> 2) + 4 * (j & 3);
+                            asm volatile("st.shared.f32 [%0], %1;\n" :: "r"(a), "f"(__ldg(f + i)) : "memory");
+                        }
+                        refine_push(p, diag, (flag_m >> j) & 1u, (uint32_t)i);
+                    }
                 }
             }
+            // the writes reach the async proxy before the TMA store reads them
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            epi_sync();
+            if (tid == 0 && ok) {
+                // (x0 < W always; a second half that would start past the image is not stored)
+                tma_store_2d(&omap, x0, y0, os);
+                if (x0 + 32 < p.W) tma_store_2d(&omap, x0 + 32, y0, os + kPIoHalf);
+                asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+            }
         }
-        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
         count_diag(diag, guarded, illcond);
     }
 
@@ -343,6 +383,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_vpass_combine_pairs(
     if (tid == 0) {
         for (int s = 0; s < S; ++s)
             if (stage_k[s] >= 0) mbar_wait_bounded(&full[s], (unsigned)((stage_k[s] / S) & 1));
+        if (*f_last >= 0) mbar_wait_bounded(ffull, (unsigned)(*f_last & 1));
         for (int b = 0; b < NB; ++b)
             if (buf_j[b] >= 0) mbar_wait_bounded(&tfull[b], (unsigned)((buf_j[b] / NB) & 1));
     }
@@ -356,29 +397,46 @@ __global__ void __launch_bounds__(kPThreads, 1) k_vpass_combine_pairs(
 // ----------------------------------------------------------------------------- host side
 size_t vp_smem_bytes(const TcGeom& g) {
     const int nb = vp_bufs(g.a);
-    return (size_t)g.vp_stages * 2 * vp_rows_in(g.a) * 128 + kPFBytes + (2 * g.vp_stages + 2 * nb) * 8 + 8 +
-           4 * (g.vp_stages + nb) + 1024;
+    return (size_t)g.vp_stages * 2 * vp_rows_in(g.a) * 128 + 2 * kPIoBytes + (2 * g.vp_stages + 2 * nb + 2) * 8 + 8 +
+           4 * (g.vp_stages + nb + 1) + 1024;
 }
 
 int vp_stages_for(int a) {
     // channel pairs need two 128-column accumulator buffers beside the Toeplitz operand and at
-    // least two stages of two channel tiles beside the staged input tile
-    if (a < 1 || a > 8 || vp_bufs(a) < 2) return 0;
+    // least two stages of two channel tiles beside the input and output tiles
+    if (a < 1 || a > 7 || vp_bufs(a) < 2) return 0;        // instantiated for a <= 7
     const size_t stage = (size_t)2 * vp_rows_in(a) * 128;
     int s = 4;
-    while (s >= 2 && (size_t)s * stage + kPFBytes + 2048 > 224 * 1024) --s;
+    while (s >= 2 && (size_t)s * stage + 2 * kPIoBytes + 256 + 1024 > kPSmemLimit) --s;
     return s >= 2 ? s : 0;
 }
 
 namespace {
 
+// f and out as 2-D FP32 tensors {W, H} with boxes {32, 128} and the 128-byte swizzle (zero fill
+// outside the image on loads; stores are clipped to it)
+cudaError_t encode_io_map(CUtensorMap* map, const float* ptr, int H, int W) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+    const cuuint64_t strides[1] = {(cuuint64_t)W * 4};
+    const cuuint32_t box[2] = {32, (cuuint32_t)PR};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <typename T, int A>
 cudaError_t launch_pairs_impl(const float* f, void* Yv, float* out, const GcParams& p, const Taps& t,
                               const TcGeom& g, DiagHeader* diag, cudaStream_t s) {
     // one box = 64 columns x 1 channel x kb_box_rows padded rows, 128-byte swizzle
-    alignas(64) CUtensorMap map;
+    alignas(64) CUtensorMap map, fmap, omap;
     cudaError_t e = encode_y_map(&map, Yv, g, p.C, std::is_same<T, __half>::value, PC, 1, g.kb_box_rows, true);
     if (e != cudaSuccess) return e;
+    if ((e = encode_io_map(&fmap, f, p.H, p.W)) != cudaSuccess) return e;
+    if ((e = encode_io_map(&omap, out, p.H, p.W)) != cudaSuccess) return e;
     const size_t smem = vp_smem_bytes(g);
     auto kern = k_vpass_combine_pairs<T, A>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -388,7 +446,7 @@ cudaError_t launch_pairs_impl(const float* f, void* Yv, float* out, const GcPara
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int tiles = (g.Wp / PC) * ((g.Hp - 2 * g.P) / PR);
     const int grid = std::max(1, std::min(tiles, sms));
-    kern<<<grid, kPThreads, smem, s>>>(map, f, out, p, t, g, diag);
+    kern<<<grid, kPThreads, smem, s>>>(map, fmap, omap, f, out, p, t, g, diag);
     return cudaGetLastError();
 }
 

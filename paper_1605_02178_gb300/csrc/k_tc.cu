@@ -295,41 +295,49 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
                     }
                 }
             }
-            // eq. (10): divided in FP32, guarded, or listed for the FP64 refinement (ratio_decision).
-            // Every pixel is stored divided first; the few guarded or listed ones are rewritten
-            // with their input value afterwards (the loads of f stay off the common path).
+            // eq. (10): every pixel is divided and stored (four at a time); pixels the cheap test
+            // (ratio_clear) does not clear take the full decision (ratio_decision) afterwards and,
+            // when guarded or listed for the FP64 refinement, are rewritten with their input
+            // value (none of either where the fit converges; the loads of f stay off this path).
             if (ok && y < p.H) {
                 float* orow = out + (size_t)y * p.W;
-                float o[16];
-                unsigned guard_m = 0, flag_m = 0;
+                unsigned odd = 0;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int how = ratio_decision(p, u[j], P_[j], Q_[j], Qa[j]);
-                    const bool in = xb + j < p.W;
-                    // 16-bit channels: a 2-ulp quotient (__fdividef) is far below their rounding
-                    o[j] = __fdividef(p.s_r * P_[j], Q_[j]) + p.t_c;
-                    illcond += in && how == 1;
-                    guard_m |= (unsigned)(in && how == 2) << j;
-                    flag_m |= (unsigned)(in && how == 3) << j;
+                for (int j0 = 0; j0 < 16; j0 += 4) {
+                    float o[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int j = j0 + e;
+                        // 16-bit channels: a 2-ulp quotient (__fdividef) is far below their rounding
+                        o[e] = __fdividef(p.s_r * P_[j], Q_[j]) + p.t_c;
+                        odd |= (unsigned)(xb + j < p.W && !ratio_clear(p, u[j], P_[j], Q_[j], Qa[j])) << j;
+                    }
+                    if (vec && xb + 16 <= p.W) {
+                        *reinterpret_cast<float4*>(orow + xb + j0) = make_float4(o[0], o[1], o[2], o[3]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (xb + j0 + e < p.W) orow[xb + j0 + e] = o[e];
+                    }
                 }
-                if (vec && xb + 16 <= p.W) {
+                if (__any_sync(__activemask(), odd != 0)) {
+                    unsigned redo = 0, flag_m = 0;
 #pragma unroll
-                    for (int j = 0; j < 16; j += 4)
-                        *reinterpret_cast<float4*>(orow + xb + j) = make_float4(o[j], o[j + 1], o[j + 2], o[j + 3]);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (xb + j < p.W) orow[xb + j] = o[j];
-                }
-                // (none of either where the fit converges)
-                if (__any_sync(__activemask(), (guard_m | flag_m) != 0)) {
-                    guarded += __popc(guard_m);
+                    for (int j = 0; j < 16; ++j) {
+                        if ((odd >> j) & 1u) {
+                            const int how = ratio_decision(p, u[j], P_[j], Q_[j], Qa[j]);
+                            illcond += how == 1;
+                            guarded += how == 2;
+                            redo |= (unsigned)(how >= 2) << j;
+                            flag_m |= (unsigned)(how == 3) << j;
+                        }
+                    }
 #pragma unroll 1
-                    for (int j = 0; j < 16; ++j)
-                        if (((guard_m | flag_m) >> j) & 1u) orow[xb + j] = __ldg(f + (size_t)y * p.W + xb + j);
-#pragma unroll 1
-                    for (int j = 0; j < 16; ++j)
-                        refine_push(p, diag, (flag_m >> j) & 1u, (uint32_t)((size_t)y * p.W + xb + j));
+                    for (int j = 0; j < 16; ++j) {
+                        const size_t i = (size_t)y * p.W + xb + j;
+                        if ((redo >> j) & 1u) orow[xb + j] = __ldg(f + i);
+                        refine_push(p, diag, (flag_m >> j) & 1u, (uint32_t)i);
+                    }
                 }
             }
         }
@@ -355,12 +363,6 @@ __global__ void __launch_bounds__(kVThreads, 1) k_vpass_combine_umma(
 }
 
 // ----------------------------------------------------------------------------- host side
-namespace {
-
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
 EncodeTiledFn encode_fn() {
     static EncodeTiledFn fn = nullptr;
     static std::once_flag once;
@@ -373,6 +375,8 @@ EncodeTiledFn encode_fn() {
     });
     return fn;
 }
+
+namespace {
 
 size_t vu_smem_bytes(const TcGeom& g) {
     const int nb = vu_bufs(g.a);
@@ -480,7 +484,9 @@ bool tc_supported(int R, int C) {
 
 cudaError_t launch_vpass_combine_tc(const float* f, void* Y, float* out, const GcParams& p, const Taps& t,
                                     const TcGeom& g, bool fp16, DiagHeader* diag, cudaStream_t s) {
-    if (g.vp_stages >= 2) return launch_vpass_combine_pairs(f, Y, out, p, t, g, fp16, diag, s);
+    // channel pairs with TMA input / output tiles (rows of f and out a multiple of 16 bytes);
+    // otherwise one channel per step
+    if (g.vp_stages >= 2 && (p.W & 3) == 0) return launch_vpass_combine_pairs(f, Y, out, p, t, g, fp16, diag, s);
     return fp16 ? launch_vpass_a<__half>(f, Y, out, p, t, g, diag, s)
                 : launch_vpass_a<__nv_bfloat16>(f, Y, out, p, t, g, diag, s);
 }

@@ -126,6 +126,8 @@ void refit(bf_gc_plan_s* p) {
     g.flag_rel = kFlagRelFp32;
     g.flag_abs = 0.0f;
     g.flag_abs_sum = 0.0f;
+    g.flag_abs0 = 0.0f;
+    g.clear_rel = (float)kIllcondRel;
     g.guard_rel = kGuardRel32;
     g.wait_ns = (unsigned long long)(p->wait_us * 1000.0);
     g.stall = p->stall;
@@ -413,6 +415,8 @@ bf_status bf_gc_forward(bf_gc_plan_t p, const float* f, float* out, void* ws, si
         for (int n = 0; n <= p->N; ++n) a1 += fabs((double)gp.coef[n]);
         gp.flag_abs = p->precision == BF_PREC_FP16 ? kFlagAbsFp16 : kFlagAbsFp32;
         gp.flag_abs_sum = (float)(gp.flag_abs * a1);
+        gp.flag_abs0 = gp.flag_abs * fabsf(gp.coef[0]);
+        gp.clear_rel = gp.flag_rel;
     }
     switch (p->form) {
     case BF_FORM_PLAIN: {
