@@ -28,7 +28,8 @@ struct TcGeom {
     // tcgen05 row pass with the Toeplitz operand in tensor memory (k_rows_tc.cu)
     int r_rows;       // padded rows per tile: floor(128 / C) (fewer if the octets do not fit)
     int r_stages;     // channel-buffer ring depth (2 .. 4)
-    int r_stg;        // staging tiles of the drain's TMA stores (1 or 2)
+    int r_stg;        // staging tiles of the drain's TMA stores (1 .. 3)
+    int r_np;         // product rows per tile (the MMA's N): r_rows C rounded up to 16
     // column pass with channel pairs (k_cols_tc.cu); 0 when a > 7 (one channel per step, k_tc.cu)
     int vp_stages;    // ring depth, stages of two channel tiles (2 .. 4)
 };
@@ -40,8 +41,8 @@ bool tc_supported(int R, int C);
 size_t umma_smem_bytes(const TcGeom& g);
 int umma_max_octets();
 int rows_tc_max_octets();
-size_t rows_tc_stage_bytes(int a);
-size_t rows_tc_stg_bytes();
+size_t rows_tc_stage_bytes(int a, int np);
+size_t rows_tc_stg_bytes(int np);
 size_t rows_tc_smem_bytes(const TcGeom& g);
 // The driver's cuTensorMapEncodeTiled, looked up once (null if unavailable)
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,

@@ -54,9 +54,9 @@ constexpr int kRGroups = kRGenWarps / kRGroupWarps;
 constexpr int kRGroupThreads = 32 * kRGroupWarps;
 constexpr int kROctSlots = 4;                     // 8-column octets per build thread per tile
 constexpr int kRTile = 128;                       // output columns per tile (accumulator lanes)
-constexpr int kRN = 128;                          // product rows per tile (accumulator columns)
-constexpr int kRStageBytesPerKb = kRN * 128;      // one 64-column K-block of B
-constexpr int kRStgBytes = kRN * kRTile * 2;      // one staging tile [128][128] of 16-bit values
+constexpr int kRN = 128;                          // accumulator columns per buffer
+// NP = TR C rounded up to 16 (<= 128) product rows per tile (the MMA's N): a K-block of B is NP
+// rows of 128 bytes, a staging tile NP rows of 128 columns (two halves of NP 128-byte rows)
 constexpr unsigned kRFlag = 4u;                   // error flag of this kernel's waits
 
 // Explicit shared-memory stores (32-bit shared-window addresses), so that no store goes through
@@ -85,9 +85,12 @@ __device__ __forceinline__ void tmem_ld_16x256b_x8(uint32_t taddr, uint32_t* v) 
 // Four 8x8 matrices of 16-bit values, stored transposed: smem row i of matrix k (address from
 // thread 8k + i) receives column i of the matrix whose row t/4, columns 2(t%4), 2(t%4) + 1 are
 // in register k of thread t
-__device__ __forceinline__ void stmatrix_x4_trans(uint32_t addr, uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3) {
-    asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1, %2, %3, %4};\n"
-                 :: "r"(addr), "r"(r0), "r"(r1), "r"(r2), "r"(r3) : "memory");
+// (executed when `on` is non-zero: a warp-uniform predicate, no branch)
+__device__ __forceinline__ void stmatrix_x4_trans(uint32_t addr, uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3,
+                                                  uint32_t on) {
+    asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %5, 0;\n"
+                 " @q stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1, %2, %3, %4};\n}\n"
+                 :: "r"(addr), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(on) : "memory");
 }
 
 __device__ __forceinline__ void drain_sync() { asm volatile("bar.sync 1, %0;\n" :: "n"(32 * kRDrainWarps) : "memory"); }
@@ -95,7 +98,7 @@ __device__ __forceinline__ void drain_sync() { asm volatile("bar.sync 1, %0;\n" 
 }  // namespace
 
 // Shared layout (1024-byte aligned): S stages of KB K-blocks | NS staging tiles | full[S] |
-// empty[S] | dfull[2] | dempty[2] | staged[2] | freed[2] | TMEM slot | abort flag | last tile
+// empty[S] | dfull[2] | dempty[2] | staged[NS] | freed[NS] | TMEM slot | abort flag | last tile
 // committed per accumulator buffer [2] | taps [kTapsSmem].
 template <typename T, int A_>
 __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_constant__ CUtensorMap ymap,
@@ -105,21 +108,21 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
     unsigned char* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
     constexpr int a = A_, KIN = kRTile + 32 * A_, KS = KIN / 16, KB = (KIN + 63) / 64, NO = KIN / 8;
     constexpr int ACOLS = KIN / 2;                     // tensor-memory columns of A
-    constexpr uint32_t SB = (uint32_t)KB * kRStageBytesPerKb;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int C = p.C, TR = g.r_rows, S = g.r_stages, NS = g.r_stg, M = TR * C;
+    const int C = p.C, TR = g.r_rows, S = g.r_stages, NS = g.r_stg, M = TR * C, NP = g.r_np;
+    const uint32_t SBk = (uint32_t)NP * 128u, SB = (uint32_t)KB * SBk, STG = (uint32_t)NP * 256u;
     unsigned char* stages = smem;
     unsigned char* stg = smem + (size_t)S * SB;
-    uint64_t* full = reinterpret_cast<uint64_t*>(stg + (size_t)NS * kRStgBytes);
+    uint64_t* full = reinterpret_cast<uint64_t*>(stg + (size_t)NS * STG);
     uint64_t* empty = full + S;
     uint64_t* dfull = empty + S;
     uint64_t* dempty = dfull + 2;
     uint64_t* staged = dempty + 2;                 // staging tile b holds a whole tile (8 drain warps)
-    uint64_t* freed = staged + 2;                  // its TMA store has read staging tile b
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(freed + 2);
+    uint64_t* freed = staged + NS;                 // its TMA store has read staging tile b
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(freed + NS);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     volatile int* last_d = abort_flag + 1;
-    float* s_g = reinterpret_cast<float*>(smem + (size_t)S * SB + (size_t)NS * kRStgBytes + (2 * S + 8) * 8 + 32);
+    float* s_g = reinterpret_cast<float*>(smem + (size_t)S * SB + (size_t)NS * STG + (2 * S + 4 + 2 * NS) * 8 + 32);
     const int tiles_x = (g.Wp + kRTile - 1) / kRTile, tiles_y = (g.Hp + TR - 1) / TR;
     const int ntiles = tiles_x * tiles_y, G = gridDim.x;
     const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;
@@ -167,7 +170,7 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
     };
     if (is_build && grp < NG) load_f((int)blockIdx.x + grp * G);
 
-    // ---- set-up: TMEM, barriers, row table, zero product rows M .. 127 of every stage
+    // ---- set-up: TMEM, barriers, row table, zero product rows M .. NP - 1 of every stage
     if (warp == kRMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" :: "r"(su32(tslot)), "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
@@ -180,19 +183,21 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
         for (int d = 0; d < 2; ++d) {
             mbar_init(&dfull[d], 1);
             mbar_init(&dempty[d], kRDrainWarps);
-            mbar_init(&staged[d], kRDrainWarps);
-            mbar_init(&freed[d], 1);
             last_d[d] = -1;
+        }
+        for (int b = 0; b < NS; ++b) {
+            mbar_init(&staged[b], kRDrainWarps);
+            mbar_init(&freed[b], 1);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     for (int j = tid; j <= t.R; j += blockDim.x) s_g[j] = t.g[j];
-    for (int idx = tid; idx < S * (kRN - M) * KB * 8; idx += blockDim.x) {      // 16-byte chunks
-        const int s = idx / ((kRN - M) * KB * 8), rem = idx % ((kRN - M) * KB * 8);
+    for (int idx = tid; idx < S * (NP - M) * KB * 8; idx += blockDim.x) {      // 16-byte chunks
+        const int s = idx / ((NP - M) * KB * 8), rem = idx % ((NP - M) * KB * 8);
         const int row = M + rem / (KB * 8), ch = rem % (KB * 8);
         const int kb = ch >> 3, c16 = ch & 7;
-        *reinterpret_cast<uint4*>(stages + (size_t)s * SB + (uint32_t)kb * kRStageBytesPerKb + (row >> 3) * 1024 +
+        *reinterpret_cast<uint4*>(stages + (size_t)s * SB + (uint32_t)kb * SBk + (row >> 3) * 1024 +
                                   (row & 7) * 128 + ((c16 ^ (row & 7)) << 4)) = make_uint4(0, 0, 0, 0);
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -253,7 +258,7 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
                 // product row m of a 128-row K-block starts at byte 128 m; its 16-byte chunk
                 // `chunk` sits at chunk ^ (m & 7) (128-byte swizzle)
                 int mrow = r * C;
-                const uint32_t Bk = su32(B) + (uint32_t)(k0 >> 6) * kRStageBytesPerKb;
+                const uint32_t Bk = su32(B) + (uint32_t)(k0 >> 6) * SBk;
 #pragma unroll 4
                 for (int c = 0; c < C; ++c, ++mrow) {
                     uint4 w;
@@ -288,7 +293,7 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
             // D f32 (bit 4); A, B f16 (0) or bf16 (1) at bits 7, 10; both K-major (bits 15, 16
             // zero); N / 8 at bit 17, M / 16 at bit 24
             const uint32_t fmt = std::is_same<T, __half>::value ? 0u : 1u;
-            const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kRN >> 3) << 17) |
+            const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(NP >> 3) << 17) |
                                    ((uint32_t)(kRTile >> 4) << 24);
             for (int it = 0; it < my_tiles; ++it) {
                 const int s = it % S, use = it / S, d = it & 1, duse = it >> 1;
@@ -301,9 +306,9 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
 #pragma unroll
                 for (int ks = 0; ks < KS; ++ks) {
                     // A: 8 tensor-memory columns per k-step; B: 32 bytes per k-step inside a
-                    // 64-column K-block, K-blocks kRStageBytesPerKb apart
+                    // 64-column K-block, K-blocks SBk apart
                     const uint64_t bd =
-                        b0 + (uint64_t)(((uint32_t)(ks >> 2) * kRStageBytesPerKb + (uint32_t)(ks & 3) * 32u) >> 4);
+                        b0 + (uint64_t)(((uint32_t)(ks >> 2) * SBk + (uint32_t)(ks & 3) * 32u) >> 4);
                     asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
                                  " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, q;\n}\n"
                                  :: "r"(dt), "r"(tbase + (uint32_t)(8 * ks)), "l"(bd), "r"(idesc),
@@ -329,21 +334,28 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
                     break;
                 const int tile = (int)blockIdx.x + it * G;
                 const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
-                unsigned char* sb = stg + (size_t)b * kRStgBytes;
+                unsigned char* sb = stg + (size_t)b * STG;
                 for (int hh = 0; hh < 2; ++hh) {
                     const int xs = tx * kRTile + 64 * hh;
                     if (xs >= g.Wp) break;
                     asm volatile(
                         "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];\n"
                         :: "l"(reinterpret_cast<uint64_t>(&ymap)), "r"(xs), "r"(0), "r"(ty * TR),
-                           "r"(su32(sb) + (uint32_t)hh * (kRStgBytes / 2))
+                           "r"(su32(sb) + (uint32_t)hh * (STG / 2))
                         : "memory");
                 }
                 asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
-                // the store of tile it - (NS - 1) has read its staging tile
-                if (NS > 1) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
-                else asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
-                mbar_arrive(&freed[(it - (NS - 1)) % NS]);
+                // free a staging tile once its store has read it.  Two staging tiles: wait for this
+                // tile's store (the drain of tile it + 1 fills the other one meanwhile).  Three or
+                // more: keep two stores in flight and free the previous tile's (the drain of tile
+                // it + NS - 1 waits for it; it has tiles it + 1 .. it + NS - 2 to fill meanwhile)
+                if (NS >= 3) {
+                    asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+                    if (it >= 1) mbar_arrive(&freed[(it - 1) % NS]);
+                } else {
+                    asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+                    mbar_arrive(&freed[b]);
+                }
             }
             asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
         }
@@ -364,7 +376,7 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
         };
         for (int it = 0; it < my_tiles; ++it) {
             const int d = it & 1, duse = it >> 1, b = it % NS;
-            unsigned char* sb = stg + (size_t)b * kRStgBytes;
+            unsigned char* sb = stg + (size_t)b * STG;
             if (!wait_warp(&dfull[d], (unsigned)(duse & 1))) break;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             // lanes 32q .. 32q + 15 (L = 0) and 32q + 16 .. 32q + 31 (L = 1), columns 64h .. 64h + 63
@@ -382,7 +394,7 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
             // (rows from M on are never stored)
             auto stage = [&](const uint32_t* v, int L) {
                 const int xb = 32 * q + 16 * L + 8 * (mk & 1);       // first column of matrix mk
-                const uint32_t half = su32(sb) + (uint32_t)(xb >> 6) * (kRStgBytes / 2);
+                const uint32_t half = su32(sb) + (uint32_t)(xb >> 6) * (STG / 2);
                 const int j = (xb & 63) >> 3;
 #pragma unroll
                 for (int i = 0; i < 8; i += 2) {
@@ -392,7 +404,8 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
                                       pack2<T>(__uint_as_float(v[4 * i]), __uint_as_float(v[4 * i + 1])),
                                       pack2<T>(__uint_as_float(v[4 * i + 2]), __uint_as_float(v[4 * i + 3])),
                                       pack2<T>(__uint_as_float(v[4 * i + 4]), __uint_as_float(v[4 * i + 5])),
-                                      pack2<T>(__uint_as_float(v[4 * i + 6]), __uint_as_float(v[4 * i + 7])));
+                                      pack2<T>(__uint_as_float(v[4 * i + 6]), __uint_as_float(v[4 * i + 7])),
+                                      64 * h + 8 * i < NP);           // rows NP .. 127 are not staged
                 }
             };
             stage(v0, 0);
@@ -421,12 +434,13 @@ __global__ void __launch_bounds__(kRThreads, 1) k_build_hpass_tc(const __grid_co
 
 int rows_tc_max_octets() { return kRGroupThreads * kROctSlots; }
 
-size_t rows_tc_stage_bytes(int a) { return (size_t)((kRTile + 32 * a + 63) / 64) * kRStageBytesPerKb; }
+size_t rows_tc_stage_bytes(int a, int np) { return (size_t)((kRTile + 32 * a + 63) / 64) * np * 128; }
 
-size_t rows_tc_stg_bytes() { return kRStgBytes; }
+size_t rows_tc_stg_bytes(int np) { return (size_t)np * kRTile * 2; }
 
 size_t rows_tc_smem_bytes(const TcGeom& g) {
-    return (size_t)g.r_stages * rows_tc_stage_bytes(g.a) + (size_t)g.r_stg * kRStgBytes + (2 * g.r_stages + 8) * 8 +
+    return (size_t)g.r_stages * rows_tc_stage_bytes(g.a, g.r_np) + (size_t)g.r_stg * rows_tc_stg_bytes(g.r_np) +
+           (2 * g.r_stages + 4 + 2 * g.r_stg) * 8 +
            32 + kTapsSmem * 4 + 1024;
 }
 

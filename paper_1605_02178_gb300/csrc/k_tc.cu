@@ -460,12 +460,13 @@ TcGeom tc_geometry(int H, int W, int R, int C, int tw) {
     g.u_kbb = (64 + 32 * g.a + 63) / 64;
     g.r_rows = std::max(1, std::min(128 / std::max(1, C), rows_tc_max_octets() / ((128 + 32 * g.a) / 8)));
     // ring depth and staging tiles of the tensor-memory row pass within 224 KB of shared memory
-    static const int kChoices[6][2] = {{4, 2}, {3, 2}, {4, 1}, {3, 1}, {2, 2}, {2, 1}};
+    g.r_np = std::min(128, (g.r_rows * C + 15) / 16 * 16);
+    static const int kChoices[8][2] = {{3, 2}, {4, 2}, {3, 3}, {2, 3}, {4, 1}, {3, 1}, {2, 2}, {2, 1}};
     g.vp_stages = vp_stages_for(g.a);
     g.r_stages = 0;
     g.r_stg = 0;
     for (const auto& c : kChoices)
-        if ((size_t)c[0] * rows_tc_stage_bytes(g.a) + (size_t)c[1] * rows_tc_stg_bytes() <= 224 * 1024) {
+        if ((size_t)c[0] * rows_tc_stage_bytes(g.a, g.r_np) + (size_t)c[1] * rows_tc_stg_bytes(g.r_np) <= 224 * 1024) {
             g.r_stages = c[0];
             g.r_stg = c[1];
             break;
