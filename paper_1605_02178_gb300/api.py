@@ -1,8 +1,15 @@
 """User-facing wrappers over the C-ABI binding: a plan object, the filter call, and the
 torch.autograd.Function that routes gradients through the library's adjoint."""
+import warnings
+
 import torch
 
 from . import bfgc as B
+
+# A range-kernel fit whose worst error reaches this (the Gaussian range kernel itself is at
+# most 1) does not approximate the filter: the degree N is too low for exp on [-mu, mu],
+# mu = ((U - L) / 2)^2 / sigma_r^2 (about e mu / 2 is needed)
+FIT_DIVERGES = 1.0
 
 
 class GCPlan:
@@ -32,6 +39,11 @@ class GCPlan:
         self.form, self.precision, self.poly, self.tile_w = form, precision, poly, tile_w
         self.save_channels = bool(save_channels)
         self._ws = {}
+        fit = self.info["fit_err"]
+        if not fit < FIT_DIVERGES:
+            warnings.warn(f"GCPlan: the degree-{N} fit of the range kernel at sigma_r={sigma_r} has worst error "
+                          f"{fit:.3g}: the output does not approximate the bilateral filter; raise N",
+                          RuntimeWarning, stacklevel=2)
 
     def __del__(self):
         if getattr(self, "handle", None) is not None:

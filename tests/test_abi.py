@@ -191,3 +191,17 @@ def test_wait_stall_and_refine_options_are_checked():
         assert B.bf_gc_workspace_size(p)[0] == with_list - 64 * 64 * 4
     finally:
         B.bf_gc_plan_destroy(p)
+
+
+def test_plan_warns_when_the_range_fit_diverges():
+    """A degree too low for exp on [-mu, mu] gives a kernel off by orders of magnitude: the
+    plan says so; a convergent fit (sigma_r = 50, N = 20) stays silent."""
+    import warnings
+    from paper_1605_02178_gb300 import api
+    with pytest.warns(RuntimeWarning, match="raise N"):
+        p = api.GCPlan(64, 64, 3.0, 10.0, 5)
+    assert p.info["fit_err"] >= api.FIT_DIVERGES
+    with warnings.catch_warnings():
+        warnings.simplefilter("error")
+        q = api.GCPlan(64, 64, 3.0, 50.0, 20)
+    assert q.info["fit_err"] < 1e-6
