@@ -826,6 +826,32 @@ def run_batch_study(args, dev):
     line("batch graph, fused_tc bf16, autotuned", ms, branches=bt.branches, tile_w_images=widths,
          tuning_s=round(tune_s, 1), bit_exact_vs_per_image=f"{same}/{len(specs)}",
          maxabs_vs_fp64_oracle_sampled=worst, oracle_images=checked, oracle_samples=8 * checked)
+    del bt
+    torch.cuda.empty_cache()
+    # one persistent launch per pass over the (image, tile) work list (the batch's a for every
+    # image, FP32 guard): against the per-image forwards and the oracle at convergent images
+    for prec in ("bf16", "fp16"):
+        bt = GCBatch(specs, form="fused_tc", precision=prec, mode="persistent")
+        ms = timed(lambda: bt.forward(fs, outs, stream))
+        d = bt.diagnostics(stream)
+        rng = np.random.default_rng(11)
+        worst, worst_pi, checked = 0.0, 0.0, 0
+        for s, f, o, r_tc in zip(specs, fs, outs, ref):
+            if api.GCPlan(s["H"], s["W"], s["sigma_s"], s["sigma_r"], s["N"]).info["fit_err"] > 1e-2:
+                continue
+            idx = rng.integers(0, s["H"] * s["W"], 8)
+            r = oracle.gcf_at(f.cpu().numpy(), idx, s["sigma_s"], s["sigma_r"], s["N"])
+            worst = max(worst, float(np.abs(o.cpu().numpy().reshape(-1)[idx] - r).max()))
+            if prec == "bf16":
+                worst_pi = max(worst_pi, float((o - r_tc).abs().max()))
+            checked += 1
+        line(f"persistent, fused_tc {prec}", ms, launches_per_batch=2, a=bt.plans and max(
+             (p.info["R"] + 15) // 16 for p in bt.plans), error_flags=d["error_flags"],
+             maxabs_vs_per_image_bf16=worst_pi if prec == "bf16" else None,
+             maxabs_vs_fp64_oracle_sampled=worst, oracle_images=checked, oracle_samples=8 * checked,
+             workspace_mb=bt.ws.numel() / 2 ** 20)
+        del bt
+        torch.cuda.empty_cache()
 
 
 def main():

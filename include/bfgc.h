@@ -277,8 +277,22 @@ typedef struct bf_gc_batch_s *bf_gc_batch_t;
  * enabled are refused (BF_ERR_INVALID_ARG). */
 bf_status bf_gc_batch_create(int count, const bf_gc_plan_t *plans, int branches, bf_gc_batch_t *out);
 
+/* Persistent mode of a batch of tensor-core plans: bf_gc_batch_forward then runs ONE launch
+ * of a batched row pass and ONE launch of a batched column pass over a device work list of
+ * (image, tile) items (both captured in a CUDA graph), instead of per-image launches.  Every
+ * plan must have form BF_FORM_FUSED_TC with the same precision (BF16 or FP16), the default
+ * row-pass tile (BF_OPT_TILE_W 0) and R <= 64; otherwise BF_ERR_UNSUPPORTED.  Each image is
+ * filtered at the batch's largest window block count a = ceil(R / 16) with its own taps (zero
+ * beyond its R), so its result equals its own forward up to the FP32 summation order of the
+ * banded products; the division of eq. (10) takes the FP32 guard (no FP64 refinement).  The
+ * counters of all images (n_guarded, n_illcond, error_flags) land in the workspace header:
+ * bf_gc_diagnostics with any of the batch's plans reads them.  Allocates the device work
+ * list (a few KB per image) and a pinned host copy of it; 1 <= count <= 65536. */
+bf_status bf_gc_batch_create_persistent(int count, const bf_gc_plan_t *plans, bf_gc_batch_t *out);
+
 /* Workspace bytes for bf_gc_batch_forward: the sum over branches of the largest forward
- * workspace among the branch's images (each rounded up to 256 bytes).  Host only. */
+ * workspace among the branch's images (each rounded up to 256 bytes); in persistent mode a
+ * 256-byte header and every image's channel buffer.  Host only. */
 bf_status bf_gc_batch_workspace_size(bf_gc_batch_t batch, size_t *bytes);
 
 /* The branch (0 .. branches-1) of image i in branch_of[i] (count entries, may be NULL) and

@@ -1,10 +1,13 @@
 """Batches of independent images, each with its own size, sigma_s, sigma_r and N, filtered
 as one CUDA graph through bf_gc_batch_* (include/bfgc.h).
 
-The paper filters one image at a time (Sec. III); a batch runs the same per-image method,
-so every image's result equals that of a single bf_gc_forward with the same plan, bit for
-bit.  Branch counts and row-pass tile widths come from the Autotuner (autotune.py) when
-one is given.
+The paper filters one image at a time (Sec. III); a batch runs the same per-image method.
+mode="branches": per-image forwards on concurrent graph branches, so every image's result
+equals that of a single bf_gc_forward with the same plan, bit for bit; branch counts and
+row-pass tile widths come from the Autotuner (autotune.py) when one is given.
+mode="persistent" (tensor-core form): one launch of each pass over a device work list of
+(image, tile) items; each image equals its own forward up to the FP32 summation order of the
+banded products, with the FP32 guard of eq. (10) in place of the FP64 refinement.
 """
 import torch
 
@@ -23,10 +26,12 @@ class GCBatch:
     """
 
     def __init__(self, specs, form="fused_tc", precision="bf16", poly="chebyshev", branches=None,
-                 tuner=None, device=None):
+                 tuner=None, device=None, mode="branches"):
         if not specs:
             raise ValueError("empty batch")
-        self.form, self.precision, self.poly = form, precision, poly
+        if mode not in ("branches", "persistent"):
+            raise ValueError(f"mode {mode!r}: 'branches' or 'persistent'")
+        self.form, self.precision, self.poly, self.mode = form, precision, poly, mode
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.tuner = tuner
         self.plans = []
@@ -34,7 +39,7 @@ class GCBatch:
             tw = int(s.get("tile_w", 0))
             plan = GCPlan(s["H"], s["W"], s["sigma_s"], s["sigma_r"], s["N"], form=form, precision=precision,
                           poly=poly)
-            if tw == 0 and tuner is not None and form == "fused_tc":
+            if tw == 0 and tuner is not None and form == "fused_tc" and mode == "branches":
                 info = plan.info
                 tw = tuner.tile_w(info["R"], info["C"], s["W"], precision)
             if tw:
@@ -44,13 +49,16 @@ class GCBatch:
         self.handle = None
         self.ws = None
         self._make(DEFAULT_BRANCHES if branches is None else int(branches))
-        self._tuned = branches is not None or tuner is None
+        self._tuned = branches is not None or tuner is None or mode == "persistent"
 
     def _make(self, branches):
         if self.handle is not None:
             B.bf_gc_batch_destroy(self.handle)
             self.handle = None
-        self.handle = B.bf_gc_batch_create([p.handle for p in self.plans], branches)
+        if self.mode == "persistent":
+            self.handle = B.bf_gc_batch_create_persistent([p.handle for p in self.plans])
+        else:
+            self.handle = B.bf_gc_batch_create([p.handle for p in self.plans], branches)
         self.branches = branches
         need = max(B.bf_gc_batch_workspace_size(self.handle), 256)
         if self.ws is None or self.ws.numel() < need:
@@ -68,6 +76,10 @@ class GCBatch:
     @property
     def pixels(self):
         return sum(p.H * p.W for p in self.plans)
+
+    def diagnostics(self, stream=None):
+        """Counters of the last forward (persistent mode: all images together)."""
+        return self.plans[0].diagnostics(self.ws, stream)
 
     def info(self):
         """(branch of each image, CUDA graphs captured so far)."""

@@ -67,6 +67,7 @@ SIGNATURES = {
     "bf_gc_profile_enable": (_I, [_P, _I]),
     "bf_gc_profile_read": (_I, [_P, ctypes.POINTER(bf_kernel_time), _I, ctypes.POINTER(_I)]),
     "bf_gc_batch_create": (_I, [_I, ctypes.POINTER(_P), _I, ctypes.POINTER(_P)]),
+    "bf_gc_batch_create_persistent": (_I, [_I, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "bf_gc_batch_workspace_size": (_I, [_P, ctypes.POINTER(_SZ)]),
     "bf_gc_batch_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "bf_gc_batch_forward": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P, _SZ, _P]),
@@ -261,6 +262,13 @@ def bf_gc_batch_create(plans, branches):
     arr = (_P * len(plans))(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in plans])
     h = ctypes.c_void_p()
     _check(lib().bf_gc_batch_create(len(plans), arr, int(branches), ctypes.byref(h)), "bf_gc_batch_create")
+    return h
+
+
+def bf_gc_batch_create_persistent(plans):
+    arr = (_P * len(plans))(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in plans])
+    h = ctypes.c_void_p()
+    _check(lib().bf_gc_batch_create_persistent(len(plans), arr, ctypes.byref(h)), "bf_gc_batch_create_persistent")
     return h
 
 
