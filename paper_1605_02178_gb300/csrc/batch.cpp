@@ -63,10 +63,6 @@ void release_graph(bf_gc_batch_s* b) {
     b->exec = nullptr;
 }
 
-// Work-list chunks: CTA b of a persistent batched pass takes chunks b, b + grid, ... of this
-// many consecutive items (row-pass tiles, column-pass tiles)
-constexpr int kRowChunk = 4, kColChunk = 1;
-
 // The Toeplitz words of an image (BatchImg::tt) in the channel storage's 16-bit format:
 // tt[p][t] = (g(s - P), g(s + 1 - P)), s = 2t - 128 + p, g(d) = taps[|d|] for |d| <= R, else 0
 void pack_toeplitz(bfgc::BatchImg& im, const float* taps, int R, int P, bool fp16) {
@@ -135,8 +131,6 @@ bf_status persistent_forward(bf_gc_batch_s* b, const float* const* d_f, float* c
     wc.item0 = (const int*)(t + o_col0);
     wr.total = b->row0[count];
     wc.total = b->col0[count];
-    wr.chunk = kRowChunk;
-    wc.chunk = kColChunk;
     DiagHeader* diag = (DiagHeader*)d_ws;
     if (b->streams.empty()) {
         b->streams.assign(1, nullptr);
@@ -267,8 +261,8 @@ bf_status bf_gc_batch_create_persistent(int count, const bf_gc_plan_t* plans, bf
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     sms = std::max(sms, 1);
-    b->grid_rows = (int)std::min<long long>(sms, (rows_total + kRowChunk - 1) / kRowChunk);
-    b->grid_cols = (int)std::min<long long>(sms, (cols_total + kColChunk - 1) / kColChunk);
+    b->grid_rows = (int)std::min<long long>(sms, (rows_total + bfgc::kBatchRowChunk - 1) / bfgc::kBatchRowChunk);
+    b->grid_cols = (int)std::min<long long>(sms, (cols_total + bfgc::kBatchColChunk - 1) / bfgc::kBatchColChunk);
     b->tab_bytes = sizeof(bfgc::BatchImg) * count + sizeof(int) * (b->row0.size() + b->col0.size());
     if (cudaMalloc(&b->d_tab, b->tab_bytes) != cudaSuccess || cudaMallocHost(&b->h_tab, b->tab_bytes) != cudaSuccess) {
         bf_gc_batch_destroy(b);

@@ -37,15 +37,17 @@ struct BatchImg {
 
 // A launch's view of the work list: items of image i are item0[i] .. item0[i + 1] - 1 (row-pass
 // tiles or column-pass tiles in the per-image kernels' order), `total` in all.  The list is cut
-// into chunks of `chunk` consecutive items; CTA b takes chunks b, b + grid, b + 2 grid, ...,
+// into chunks of consecutive items (kBatchRowChunk, kBatchColChunk); CTA b takes chunks b, b + grid, b + 2 grid, ...,
 // so that the CTAs work on neighbouring tiles at the same time (shared halo rows meet in L2,
 // and the writes stay in a narrow address range).
 struct BatchWork {
     const BatchImg* imgs;
     const int* item0;
-    int nimg, total, chunk;
+    int nimg, total;
     unsigned long long wait_ns;
 };
+// Chunk sizes of the two passes' work lists (consecutive row-pass / column-pass tiles)
+constexpr int kBatchRowChunk = 4, kBatchColChunk = 1;
 
 // Shared-memory ring of the batched row pass at window block count a: stages of KB K-blocks of
 // 128 product rows, staging tiles of 128 rows (the largest product-row count of any image).

@@ -39,7 +39,7 @@ namespace {
 
 // row pass roles (as k_rows_tc.cu)
 constexpr int kBDrainWarps = 8;
-constexpr int kBGenWarps = 12;
+constexpr int kBGenWarps = 8;
 constexpr int kBMmaWarp = kBDrainWarps + kBGenWarps;          // warp 20
 constexpr int kBStoreWarp = kBMmaWarp + 1;                    // warp 21
 constexpr int kBRowThreads = 32 * (kBStoreWarp + 1);
@@ -102,11 +102,6 @@ __device__ __forceinline__ int img_find(const int* __restrict__ item0, int nimg,
     }
     return l;
 }
-// ... and from the image `cur` of an earlier item of the same walk
-__device__ __forceinline__ int img_next(const int* __restrict__ item0, int cur, int item) {
-    while (__ldg(item0 + cur + 1) <= item) ++cur;
-    return cur;
-}
 
 // A role's cursor over the images of its walk: image `cur` holds items base .. next - 1.
 // to(item) moves to the image of a later item and says whether the image changed, so that a
@@ -132,35 +127,33 @@ struct Walk {
     }
 };
 
-// The items of CTA b: chunks b, b + G, ... of K consecutive items of the list of `total`.
+// The items of CTA b: chunks b, b + G, ... of K consecutive items of the list of w.total
+// (b = blockIdx.x, G = gridDim.x); no state beyond the launch's.
+template <int K>
 struct Items {
-    int b, G, K, total, count;
-    __device__ __forceinline__ void init(const BatchWork& w) {
-        b = (int)blockIdx.x;
-        G = (int)gridDim.x;
-        K = w.chunk;
-        total = w.total;
+    static __device__ __forceinline__ int count(const BatchWork& w) {
+        const int b = (int)blockIdx.x, G = (int)gridDim.x, total = w.total;
         const int nchunks = (total + K - 1) / K;
-        if (b >= nchunks) {
-            count = 0;
-            return;
-        }
+        if (b >= nchunks) return 0;
         const int mine = (nchunks - 1 - b) / G + 1, last = b + (mine - 1) * G;
-        count = (mine - 1) * K + (last == nchunks - 1 ? total - last * K : K);
+        return (mine - 1) * K + (last == nchunks - 1 ? total - last * K : K);
     }
-    __device__ __forceinline__ int item(int it) const { return (b + (it / K) * G) * K + it % K; }
-    // the first item >= x of this CTA (total if none)
-    __device__ __forceinline__ int from(int x) const {
-        if (x >= total) return total;
+    static __device__ __forceinline__ int item(int it) {
+        return ((int)blockIdx.x + (it / K) * (int)gridDim.x) * K + it % K;
+    }
+    // the first item >= x of this CTA (w.total if none)
+    static __device__ __forceinline__ int from(const BatchWork& w, int x) {
+        const int b = (int)blockIdx.x, G = (int)gridDim.x;
+        if (x >= w.total) return w.total;
         const int cx = x / K;
         const int c = cx <= b ? b : b + (cx - b + G - 1) / G * G;
         const int it = c == cx ? x : c * K;
-        return it < total ? it : total;
+        return it < w.total ? it : w.total;
     }
     // the image of this CTA's walk after image j (nimg if none)
-    __device__ __forceinline__ int next_img(const BatchWork& w, int j) const {
-        const int x = from(__ldg(w.item0 + j + 1));
-        return x < total ? img_find(w.item0, w.nimg, x) : w.nimg;
+    static __device__ __forceinline__ int next_img(const BatchWork& w, int j) {
+        const int x = from(w, __ldg(w.item0 + j + 1));
+        return x < w.total ? img_find(w.item0, w.nimg, x) : w.nimg;
     }
 };
 
@@ -180,6 +173,20 @@ __device__ void write_toeplitz(uint32_t col, int q, int lane, const BatchImg* __
     asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
 }
 
+// The batch's guard of eq. (10) is the FP32 one of a plan without the refinement
+// (clear_rel = 1e-3, no absolute allowance, guard_rel = kGuardRel32): ratio_clear and
+// ratio_decision with those parameters, written with them as constants so that no parameter
+// is held in registers across the epilogue.
+__device__ __forceinline__ bool clear32(float u, float P, float Q, float Qa) {
+    return fabsf(u) <= 1.0f && Qa > 0.0f && Qa <= 3.0e38f && fabsf(P) <= 3.0e38f &&
+           fabsf(Q) >= (float)kIllcondRel * Qa;
+}
+__device__ __forceinline__ int decide32(float P, float Q, float Qa) {
+    const bool bad = !(Qa > 0.0f) || !(Qa <= 3.0e38f) || !(fabsf(P) <= 3.0e38f);
+    if (bad || !(fabsf(Q) >= kGuardRel32 * Qa)) return 2;
+    return fabsf(Q) < (float)kIllcondRel * Qa ? 1 : 0;
+}
+
 }  // namespace
 
 // ============================================================================= row pass
@@ -194,13 +201,12 @@ __global__ void __launch_bounds__(kBRowThreads, 1) k_rows_batch(const BatchWork 
     constexpr int ACOLS = KIN / 2;
     constexpr uint32_t SB = (uint32_t)KB * kBKb;
     static_assert(ACOLS <= 128, "two Toeplitz slots of 128 columns");
-    Items I;
-    I.init(w);
-    const int my_tiles = I.count;
+    using I = Items<kBatchRowChunk>;
+    const int my_tiles = I::count(w);
     if (my_tiles <= 0) return;                         // the whole CTA, before any set-up
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // the first two images of the walk (slots 0 and 1 of the Toeplitz operand)
-    const int img_lo = img_find(w.item0, w.nimg, I.item(0)), img_1 = I.next_img(w, img_lo);
+    const int img_lo = img_find(w.item0, w.nimg, I::item(0)), img_1 = I::next_img(w, img_lo);
     unsigned char* stages = smem;
     unsigned char* stg = smem + (size_t)S * SB;
     uint64_t* full = reinterpret_cast<uint64_t*>(stg + (size_t)NS * kBStg);
@@ -221,30 +227,20 @@ __global__ void __launch_bounds__(kBRowThreads, 1) k_rows_batch(const BatchWork 
     const int grp = (warp - kBDrainWarps) / kBGroupWarps;
     const int gtid = tid - 32 * (kBDrainWarps + kBGroupWarps * grp);
     float fv[kBOctSlots][8];
-    Walk lw;                                           // image cursor of the fetches
+    Walk lw;                                           // image cursor of the fetches and builds
     lw.init(w.item0, img_lo);
-    int lH = 0, lW = 0, lTR = 1, lHp = 0, ltx = 1;
-    const float* lf = nullptr;
-    auto load_enter = [&]() {
-        const BatchImg* im = w.imgs + lw.cur;
-        lH = im->p.H;
-        lW = im->p.W;
-        lTR = im->g.r_rows;
-        lHp = im->g.Hp;
-        ltx = (im->g.Wp + kBTile - 1) / kBTile;
-        lf = im->f;
-    };
-    load_enter();
     auto load_f = [&](int it) {
 #pragma unroll
         for (int s = 0; s < kBOctSlots; ++s)
 #pragma unroll
             for (int e = 0; e < 8; ++e) fv[s][e] = 0.0f;
         if (it >= my_tiles) return;
-        const int item = I.item(it);
-        if (lw.to(w.item0, item)) load_enter();
-        const int H = lH, W = lW, TR = lTR, Hp = lHp;
-        const float* __restrict__ f = lf;
+        const int item = I::item(it);
+        lw.to(w.item0, item);
+        const BatchImg* im = w.imgs + lw.cur;
+        const int H = im->p.H, W = im->p.W, TR = im->g.r_rows, Hp = im->g.Hp;
+        const int ltx = (im->g.Wp + kBTile - 1) / kBTile;
+        const float* __restrict__ f = im->f;
         const int lt = item - lw.base;
         const int ty = lt / ltx, tx = lt - ty * ltx;
         const int p0 = ty * TR, xs0 = tx * kBTile - PA, noct = TR * NO;
@@ -317,26 +313,15 @@ __global__ void __launch_bounds__(kBRowThreads, 1) k_rows_batch(const BatchWork 
 
     if (is_build) {
         // ------------------------------------------------------------ channel build
-        Walk bw;
-        bw.init(w.item0, img_lo);
-        int C = 0, M = 0, NP = 0, noct = 0;
-        float t_c = 0.0f, inv_sr = 0.0f, half_mu = 0.0f;
-        auto build_enter = [&]() {
-            const BatchImg* im = w.imgs + bw.cur;
-            C = im->p.C;
-            M = im->g.r_rows * C;
-            NP = im->g.r_np;
-            noct = im->g.r_rows * NO;
-            t_c = im->p.t_c;
-            inv_sr = im->p.inv_sr;
-            half_mu = im->p.half_mu;
-        };
-        build_enter();
+        // (the fetches run one tile of the group ahead on the same cursor: monotone items)
         auto build = [&](int it) -> bool {
             const int s = it % S, use = it / S;
             if (use > 0 && !mbar_wait_abort(&empty[s], (unsigned)((use - 1) & 1), abort_flag, diag, kBRowFlag, wait_ns))
                 return false;
-            if (bw.to(w.item0, I.item(it))) build_enter();
+            lw.to(w.item0, I::item(it));
+            const BatchImg* im = w.imgs + lw.cur;
+            const int C = im->p.C, M = im->g.r_rows * C, NP = im->g.r_np, noct = im->g.r_rows * NO;
+            const float t_c = im->p.t_c, inv_sr = im->p.inv_sr, half_mu = im->p.half_mu;
             const uint32_t B = su32(stages + (size_t)s * SB);
             // product rows M .. NP - 1 are read by the MMAs as zeros (an earlier image may have
             // left channels there)
@@ -407,7 +392,7 @@ __global__ void __launch_bounds__(kBRowThreads, 1) k_rows_batch(const BatchWork 
                 const int s = it % S, use = it / S, d = it & 1, duse = it >> 1;
                 if (!mbar_wait_abort(&full[s], (unsigned)(use & 1), abort_flag, diag, kBRowFlag, wait_ns)) break;
                 // the first tile of the range's image m >= 2: its Toeplitz operand is written
-                if (mw.to(w.item0, I.item(it))) {
+                if (mw.to(w.item0, I::item(it))) {
                     const int m = mw.m;
                     if (m >= 2 && !mbar_wait_abort(&tready[m & 1], (unsigned)(((m - 2) >> 1) & 1), abort_flag, diag,
                                                    kBRowFlag, wait_ns))
@@ -452,7 +437,7 @@ __global__ void __launch_bounds__(kBRowThreads, 1) k_rows_batch(const BatchWork 
             for (int it = 0; it < my_tiles; ++it) {
                 const int b = it % NS;
                 if (!mbar_wait_abort(&staged[b], (unsigned)((it / NS) & 1), abort_flag, diag, kBRowFlag, wait_ns)) break;
-                const int item = I.item(it);
+                const int item = I::item(it);
                 if (sw.to(w.item0, item)) store_enter();
                 const int lt = item - sw.base, ty = lt / tiles_x, tx = lt - ty * tiles_x;
                 const uint32_t sb = su32(stg + (size_t)b * kBStg);
@@ -496,13 +481,13 @@ __global__ void __launch_bounds__(kBRowThreads, 1) k_rows_batch(const BatchWork 
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&dempty[d]);
-            const int item = I.item(it);
+            const int item = I::item(it);
             if (dw.to(w.item0, item)) NP = w.imgs[dw.cur].g.r_np;
             const int m = dw.m;
             // the last tile of image m of the walk: every MMA of image m has completed, so its
             // Toeplitz slot takes image m + 2's operand (warps 0..3, one lane quarter each)
-            if (h == 0 && it + 1 < my_tiles && I.item(it + 1) >= dw.next) {
-                const int j2 = I.next_img(w, img_find(w.item0, w.nimg, I.item(it + 1)));
+            if (h == 0 && it + 1 < my_tiles && I::item(it + 1) >= dw.next) {
+                const int j2 = I::next_img(w, img_find(w.item0, w.nimg, I::item(it + 1)));
                 if (j2 < w.nimg) {
                     write_toeplitz(tbase + 128u * (uint32_t)(m & 1), q, lane, w.imgs + j2, ACOLS);
                     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -551,8 +536,9 @@ __global__ void __launch_bounds__(kBRowThreads, 1) k_rows_batch(const BatchWork 
 
 // ============================================================================= column pass
 // Shared layout (1024-byte aligned): S stages of two channel blocks | full[S] | empty[S] |
-// tfull[2] | tempty[2] | tready[2] | TMEM slot | abort flag | last step loaded per stage [S] |
-// last step committed per accumulator buffer [2].  Pair step k (counted over the CTA's tiles,
+// tfull[2] | tempty[2] | tready[2] | epilogue barrier | TMEM slot | abort flag | last step loaded
+// per stage [S] | last step committed per accumulator buffer [2] | the epilogue's image
+// parameters and walk.  Pair step k (counted over the CTA's tiles,
 // (C + 1) / 2 per tile of an image with C channels) uses stage k mod S and buffer k mod 2.
 template <typename T, int A_>
 __global__ void __launch_bounds__(kCThreads, 1) k_cols_batch(const BatchWork w, DiagHeader* diag, int S) {
@@ -561,23 +547,31 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cols_batch(const BatchWork w, 
     constexpr int RIN = kCRows + 32 * A_, KS = RIN / 16, SB = RIN * 128, SP = 2 * SB, PA = 16 * A_;
     constexpr int ACOLS = RIN / 2, NB = 2;
     static_assert(ACOLS <= 128, "two Toeplitz slots of 128 columns");
-    Items I;
-    I.init(w);
-    const int my_tiles = I.count;
+    using I = Items<kBatchColChunk>;
+    const int my_tiles = I::count(w);
     if (my_tiles <= 0) return;                         // the whole CTA, before any set-up
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // the first two images of the walk (slots 0 and 1 of the Toeplitz operand)
-    const int img_lo = img_find(w.item0, w.nimg, I.item(0)), img_1 = I.next_img(w, img_lo);
+    const int img_lo = img_find(w.item0, w.nimg, I::item(0)), img_1 = I::next_img(w, img_lo);
     unsigned char* stages = smem;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)S * SP);
     uint64_t* empty = full + S;
     uint64_t* tfull = empty + S;
     uint64_t* tempty = tfull + NB;
     uint64_t* tready = tempty + NB;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(tready + 2);
+    uint64_t* ebar = tready + 2;                       // the epilogue warps' barrier
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(ebar + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     volatile int* stage_k = abort_flag + 1;
     volatile int* buf_j = stage_k + S;
+    // the epilogue's copy of the current image's parameters (16-byte aligned)
+    GcParams* sp = reinterpret_cast<GcParams*>(
+        (reinterpret_cast<uintptr_t>(const_cast<int*>(buf_j + NB)) + 15) & ~(uintptr_t)15);
+    int* s_ty = reinterpret_cast<int*>(sp + 1);
+    const float** s_f = reinterpret_cast<const float**>(
+        (reinterpret_cast<uintptr_t>(s_ty + 1) + 7) & ~(uintptr_t)7);
+    float** s_out = reinterpret_cast<float**>(reinterpret_cast<uintptr_t>(s_f + 1));
+    int* s_walk = reinterpret_cast<int*>(s_out + 1);          // the epilogue's image: cur, base, next, m
     const unsigned long long wait_ns = w.wait_ns;
 
     if (warp == kCEpiWarps) {
@@ -596,6 +590,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cols_batch(const BatchWork w, 
             mbar_init(&tready[b], 4);
             buf_j[b] = -1;
         }
+        mbar_init(ebar, kCEpiWarps);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -632,7 +627,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cols_batch(const BatchWork w, 
             };
             prod_enter();
             for (int it = 0; it < my_tiles && ok; ++it) {
-                const int item = I.item(it);
+                const int item = I::item(it);
                 if (pw.to(w.item0, item)) prod_enter();
                 const int lt = item - pw.base;
                 const int x0 = (lt / tiles_y) * kCCols, y0 = (lt % tiles_y) * kCRows;
@@ -665,7 +660,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cols_batch(const BatchWork w, 
             mw.init(w.item0, img_lo);
             int CP = (w.imgs[img_lo].p.C + 1) / 2;
             for (int it = 0; it < my_tiles && ok; ++it) {
-                if (mw.to(w.item0, I.item(it))) CP = (w.imgs[mw.cur].p.C + 1) / 2;
+                if (mw.to(w.item0, I::item(it))) CP = (w.imgs[mw.cur].p.C + 1) / 2;
                 const int m = mw.m;
                 const uint32_t ab = tbase + 128u * (uint32_t)(m & 1);
                 for (int i = 0; i < CP; ++i, ++k) {
@@ -701,54 +696,76 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cols_batch(const BatchWork w, 
         }
     } else {
         // ------------------------------------------------------------ ratio epilogue
+        // The current image's parameters live in shared memory (sp), rewritten between two
+        // barriers of the 16 epilogue warps when the walk enters the next image, so that no
+        // pointer to the table is held across the pair loop.
         const int q = warp & 3, cg = warp >> 2;
         const int row = 32 * q + lane;
         const uint32_t tl = tacc + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * cg);
-        unsigned guarded = 0, illcond = 0;
         bool ok = true;
-        int k = 0;
-        Walk ew;
-        ew.init(w.item0, img_lo);
-        const BatchImg* im = w.imgs + img_lo;
-        int C = 0, CP = 0, H = 0, W = 0, tiles_y = 1;
-        float t_c = 0.0f, inv_sr = 0.0f, s_r = 0.0f;
-        auto epi_enter = [&]() {
-            im = w.imgs + ew.cur;
-            C = im->p.C;
-            CP = (C + 1) / 2;
-            H = im->p.H;
-            W = im->p.W;
-            tiles_y = (im->g.Hp - 2 * PA) / kCRows;
-            t_c = im->p.t_c;
-            inv_sr = im->p.inv_sr;
-            s_r = im->p.s_r;
+        // the epilogue warps' barrier: an mbarrier of 16 arrivals with bounded waits (a wait that
+        // runs out aborts, as every other wait here)
+        unsigned ephase = 0;
+        auto epi_sync = [&]() {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(ebar);
+            bool wt = true;
+            if (lane == 0) wt = mbar_wait_abort(ebar, ephase & 1u, abort_flag, diag, kBColFlag, wait_ns);
+            ++ephase;
+            if (!__shfl_sync(0xffffffffu, wt, 0)) ok = false;
         };
-        epi_enter();
+        // (the walk's state lives there too: every epilogue thread walks the same items)
+        auto epi_enter = [&](int cur, int m) {
+            epi_sync();                                // every warp is done with the previous image
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(&w.imgs[cur].p);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(sp);
+            for (int i = tid; i < (int)(sizeof(GcParams) / 4); i += 32 * kCEpiWarps) dst[i] = __ldg(src + i);
+            if (tid == 0) {
+                *s_ty = (w.imgs[cur].g.Hp - 2 * PA) / kCRows;
+                *s_f = w.imgs[cur].f;
+                *s_out = w.imgs[cur].out;
+                s_walk[0] = cur;
+                s_walk[1] = __ldg(w.item0 + cur);
+                s_walk[2] = __ldg(w.item0 + cur + 1);
+                s_walk[3] = m;
+            }
+            epi_sync();
+        };
+        unsigned guarded = 0, illcond = 0;
+        int k = 0;
+        epi_enter(img_lo, 0);
+        const GcParams& p = *sp;
         for (int it = 0; it < my_tiles && ok; ++it) {
-            const int item = I.item(it);
-            if (ew.to(w.item0, item)) epi_enter();
-            const GcParams& p = im->p;
-            const int m = ew.m, lt = item - ew.base;
+            const int item = I::item(it);
+            if (item >= s_walk[2]) {
+                int cur = s_walk[0];
+                do {
+                    ++cur;
+                } while (__ldg(w.item0 + cur + 1) <= item);
+                epi_enter(cur, s_walk[3] + 1);
+            }
+            const int m = s_walk[3], lt = item - s_walk[1], C = p.C, CP = (C + 1) / 2, tiles_y = *s_ty;
             const int x0 = (lt / tiles_y) * kCCols, y0 = (lt % tiles_y) * kCRows;
             const int y = y0 + row, xb = x0 + 16 * cg;
-            const float* __restrict__ f = im->f;
+            const int H = p.H, W = p.W;
             float u[16], P_[16], Q_[16], Qa[16];
-            // this thread's 16 input pixels (zero outside the image)
-            if (y < H && (W & 3) == 0 && xb + 16 <= W) {
+            // this thread's 16 input pixels (zero outside the image); converted to u once the
+            // first accumulators are in, so that the loads overlap that wait
+            {
+                const float* __restrict__ f = *s_f;
+                if (y < H && (W & 3) == 0 && xb + 16 <= W) {
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float4 v = __ldg(reinterpret_cast<const float4*>(f + (size_t)y * W + xb) + e);
-                    u[4 * e] = v.x; u[4 * e + 1] = v.y; u[4 * e + 2] = v.z; u[4 * e + 3] = v.w;
+                    for (int e = 0; e < 4; ++e) {
+                        const float4 v = __ldg(reinterpret_cast<const float4*>(f + (size_t)y * W + xb) + e);
+                        u[4 * e] = v.x; u[4 * e + 1] = v.y; u[4 * e + 2] = v.z; u[4 * e + 3] = v.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) u[j] = (y < H && xb + j < W) ? __ldg(f + (size_t)y * W + xb + j) : 0.0f;
                 }
-            } else {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) u[j] = (y < H && xb + j < W) ? __ldg(f + (size_t)y * W + xb + j) : 0.0f;
             }
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                u[j] = (u[j] - t_c) * inv_sr;
-                P_[j] = Q_[j] = Qa[j] = 0.0f;
-            }
+            for (int j = 0; j < 16; ++j) P_[j] = Q_[j] = Qa[j] = 0.0f;
             // Horner step in u over the filtered channel Z_m (see RatioAcc)
             auto horner = [&](int mc, const float* z) {
                 if (mc >= 1) {
@@ -772,6 +789,11 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cols_batch(const BatchWork w, 
                 if (lane == 0) wt = mbar_wait_abort_poll(&tfull[b], (unsigned)((k / NB) & 1), abort_flag, diag, kBColFlag, wait_ns);
                 ok = __shfl_sync(0xffffffffu, wt, 0);
                 if (!ok) break;
+                if (i == 0) {
+                    const float t_c = p.t_c, inv_sr = p.inv_sr;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) u[j] = (u[j] - t_c) * inv_sr;
+                }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 float z[16];
                 tmem_ld16(tl + (uint32_t)(b * 128), z);
@@ -785,8 +807,8 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cols_batch(const BatchWork w, 
             if (!ok) break;
             // the last tile of image m here: every MMA of image m has completed, so its Toeplitz
             // slot takes image m + 2's operand (warps 0..3, one lane quarter each)
-            if (cg == 0 && it + 1 < my_tiles && I.item(it + 1) >= ew.next) {
-                const int j2 = I.next_img(w, img_find(w.item0, w.nimg, I.item(it + 1)));
+            if (cg == 0 && it + 1 < my_tiles && I::item(it + 1) >= s_walk[2]) {
+                const int j2 = I::next_img(w, img_find(w.item0, w.nimg, I::item(it + 1)));
                 if (j2 < w.nimg) {
                     write_toeplitz(tbase + 128u * (uint32_t)(m & 1), q, lane, w.imgs + j2, ACOLS);
                     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -795,19 +817,19 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cols_batch(const BatchWork w, 
                 }
             }
             // eq. (10), un-centred; guarded pixels hold their input value.  16-byte stores where
-            // the row allows them
+            // the row allows them.  The cheap test (ratio_clear) on every pixel and the quotients
+            // stored at once; the few pixels it does not clear take the full decision
+            // (ratio_decision) afterwards and are rewritten.  (Rows past the image: nothing
+            // stored, no pixel odd; the warp vote is taken by all lanes.)
+            const float s_r = p.s_r, t_c = p.t_c;
+            float* orow = *s_out + (size_t)(y < H ? y : 0) * W;
+            unsigned odd = 0;
             if (y < H) {
-                float* orow = im->out + (size_t)y * W;
                 float o[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     o[j] = __fdividef(s_r * P_[j], Q_[j]) + t_c;
-                    if (xb + j < W && !ratio_clear(p, u[j], P_[j], Q_[j], Qa[j])) {
-                        const int how = ratio_decision(p, u[j], P_[j], Q_[j], Qa[j]);
-                        illcond += how == 1;
-                        guarded += how == 2;
-                        o[j] = how >= 2 ? __ldg(f + (size_t)y * W + xb + j) : s_r * P_[j] / Q_[j] + t_c;
-                    }
+                    odd |= (unsigned)(xb + j < W && !clear32(u[j], P_[j], Q_[j], Qa[j])) << j;
                 }
                 if ((W & 3) == 0 && xb + 16 <= W) {
 #pragma unroll
@@ -817,6 +839,26 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cols_batch(const BatchWork w, 
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
                         if (xb + j < W) orow[xb + j] = o[j];
+                }
+            }
+            if (__any_sync(0xffffffffu, odd != 0)) {
+                unsigned redo = 0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    if ((odd >> j) & 1u) {
+                        const int how = decide32(P_[j], Q_[j], Qa[j]);
+                        illcond += how == 1;
+                        guarded += how == 2;
+                        if (how < 2) orow[xb + j] = s_r * P_[j] / Q_[j] + t_c;
+                        redo |= (unsigned)(how >= 2) << j;
+                    }
+                }
+                // guarded pixels: the input value
+                const float* frow = *s_f + (size_t)(y < H ? y : 0) * W;
+#pragma unroll 1
+                for (; redo; redo &= redo - 1) {
+                    const int j = __ffs(redo) - 1;
+                    orow[xb + j] = __ldg(frow + xb + j);
                 }
             }
         }
@@ -867,13 +909,14 @@ size_t rows_batch_smem(int a) {
 
 int cols_batch_stages(int a) {
     int s = 4;
-    while (s >= 2 && (size_t)s * cols_stage_bytes(a) + 256 + 1024 > kBatchSmemLimit) --s;
+    while (s >= 2 && (size_t)s * cols_stage_bytes(a) + 256 + sizeof(GcParams) + 64 + 1024 > kBatchSmemLimit) --s;
     return s >= 2 ? s : 0;
 }
 
 size_t cols_batch_smem(int a) {
     const int S = cols_batch_stages(a);
-    return (size_t)S * cols_stage_bytes(a) + (2 * S + 6) * 8 + 8 + 4 * (S + 2) + 1024;
+    return (size_t)S * cols_stage_bytes(a) + (2 * S + 7) * 8 + 8 + 4 * (S + 2) + 16 + sizeof(GcParams) + 4 + 8 + 16 +
+           16 + 1024;
 }
 
 namespace {
