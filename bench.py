@@ -803,6 +803,13 @@ def run_batch_study(args, dev):
              workspace_mb=bt.ws.numel() / 2 ** 20)
         del bt
         torch.cuda.empty_cache()
+    # the same graph with the plans' FP64 refinement off (the persistent mode's FP32 guard):
+    # where a fit diverges the refinement recomputes most pixels of the image
+    bt = GCBatch(specs, form="fused_tc", precision="bf16", branches=8, refine=False)
+    ms = timed(lambda: bt.forward(fs, outs, stream))
+    line("batch graph, fused_tc bf16, 8 branches, refinement off", ms, workspace_mb=bt.ws.numel() / 2 ** 20)
+    del bt
+    torch.cuda.empty_cache()
     tuner = autotune.Autotuner(reps=2)
     t0 = time.time()
     bt = GCBatch(specs, form="fused_tc", precision="bf16", tuner=tuner)

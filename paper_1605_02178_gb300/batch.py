@@ -21,12 +21,12 @@ class GCBatch:
     """Owns one GCPlan per image, the bf_gc_batch_t over them and the batch workspace.
 
     specs: sequence of dicts with H, W, sigma_s, sigma_r, N and optionally tile_w (row-pass
-    tile width of the tensor-core form; 0 = default).  form, precision and poly apply to
-    every image.
+    tile width of the tensor-core form; 0 = default).  form, precision, poly and refine (the
+    plans' FP64 refinement, branches mode) apply to every image.
     """
 
     def __init__(self, specs, form="fused_tc", precision="bf16", poly="chebyshev", branches=None,
-                 tuner=None, device=None, mode="branches"):
+                 tuner=None, device=None, mode="branches", refine=True):
         if not specs:
             raise ValueError("empty batch")
         if mode not in ("branches", "persistent"):
@@ -38,7 +38,7 @@ class GCBatch:
         for s in specs:
             tw = int(s.get("tile_w", 0))
             plan = GCPlan(s["H"], s["W"], s["sigma_s"], s["sigma_r"], s["N"], form=form, precision=precision,
-                          poly=poly)
+                          poly=poly, refine=refine)
             if tw == 0 and tuner is not None and form == "fused_tc" and mode == "branches":
                 info = plan.info
                 tw = tuner.tile_w(info["R"], info["C"], s["W"], precision)
