@@ -333,6 +333,17 @@ bf_status bf_gc_profile_read(bf_gc_plan_t plan, bf_kernel_time *out, int max_ent
 bf_status bf_direct(int H, int W, double sigma_s, double sigma_r, const float *d_f,
                     float *d_out, bf_stream_t stream);
 
+/* Input check (a diagnostic; the filter itself does not call it): the range-kernel fit covers
+ * intensities in [L, U] only (Sec. III-B, the approximation interval is the centred dynamic
+ * range).  Counts, over the H x W device image d_f (row-major, float32, no alignment needed),
+ * the finite pixels outside [L, U] into d_counts[0] and the non-finite ones into
+ * d_counts[1]: d_counts is a caller-owned device array of two unsigned 64-bit integers,
+ * zeroed and then written in stream order (read them after the stream has reached that
+ * point).  Nothing traps.  BF_ERR_INVALID_ARG for H < 1, W < 1, a NULL pointer, L > U or a
+ * non-finite bound; BF_ERR_CUDA if the launch fails. */
+bf_status bf_check_range(int H, int W, double L, double U, const float *d_f, unsigned long long *d_counts,
+                         bf_stream_t stream);
+
 const char *bf_status_string(bf_status s);
 const char *bf_version(void);
 

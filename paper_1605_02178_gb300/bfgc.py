@@ -73,6 +73,7 @@ SIGNATURES = {
     "bf_gc_batch_forward": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P, _SZ, _P]),
     "bf_gc_batch_destroy": (None, [_P]),
     "bf_direct": (_I, [_I, _I, _D, _D, _P, _P, _P]),
+    "bf_check_range": (_I, [_I, _I, _D, _D, _P, _P, _P]),
     "bf_status_string": (ctypes.c_char_p, [_I]),
     "bf_version": (ctypes.c_char_p, []),
     "bf_last_cuda_error": (_I, [ctypes.POINTER(ctypes.c_char_p)]),
@@ -311,6 +312,17 @@ def bf_direct(f, sigma_s, sigma_r, out=None, stream=None):
     _check(lib().bf_direct(H, W, float(sigma_s), float(sigma_r), _ptr(f), _ptr(out), _stream(stream)),
            "bf_direct")
     return out
+
+
+def bf_check_range(f, L=0.0, U=255.0, stream=None):
+    """(pixels outside [L, U], non-finite pixels) of the device image f, after a stream sync."""
+    _dev_f32(f, "f")
+    H, W = f.shape[-2], f.shape[-1]
+    counts = torch.empty(2, dtype=torch.int64, device=f.device)
+    _check(lib().bf_check_range(H, W, float(L), float(U), _ptr(f), _ptr(counts), _stream(stream)),
+           "bf_check_range")
+    c = counts.cpu()
+    return int(c[0]), int(c[1])
 
 
 def bf_status_string(status):

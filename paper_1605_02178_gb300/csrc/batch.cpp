@@ -127,6 +127,7 @@ bf_status persistent_forward(bf_gc_batch_s* b, const float* const* d_f, float* c
     wr.imgs = wc.imgs = (const bfgc::BatchImg*)t;
     wr.nimg = wc.nimg = count;
     wr.wait_ns = wc.wait_ns = b->plans[0]->gp.wait_ns;
+    wr.stall = wc.stall = b->plans[0]->gp.stall;
     wr.item0 = (const int*)(t + o_row0);
     wc.item0 = (const int*)(t + o_col0);
     wr.total = b->row0[count];

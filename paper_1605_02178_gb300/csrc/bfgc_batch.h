@@ -45,6 +45,10 @@ struct BatchWork {
     const int* item0;
     int nimg, total;
     unsigned long long wait_ns;
+    // test of the bounded waits (BF_OPT_STALL of the first plan): 1 = the row pass's first
+    // build group never hands over its first tile, 2 = the column pass never loads its first
+    // stage; nothing asynchronous is outstanding for the withheld step
+    int stall;
 };
 // Chunk sizes of the two passes' work lists (consecutive row-pass / column-pass tiles)
 constexpr int kBatchRowChunk = 4, kBatchColChunk = 1;

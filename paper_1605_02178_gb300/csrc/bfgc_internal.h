@@ -119,6 +119,7 @@ struct Profiler {
     std::vector<double> total_ms;
     std::vector<unsigned long long> launches;
     int open = -1;               // kernel whose start mark is the last one recorded
+    bool nvtx_open = false;      // an NVTX stage range is open on the calling thread
 };
 
 // Host-side plan.
@@ -168,6 +169,8 @@ cudaError_t launch_vpass_combine_f32(const float* f, const float* Y, float* out,
                                      size_t cs, DiagHeader* diag, cudaStream_t s);
 
 // FP64 recomputation of the listed pixels (k_refine.cu)
+// counts[0] = pixels of f[0 .. n) outside [L, U] (finite), counts[1] = non-finite ones
+cudaError_t launch_check_range(const float* f, size_t n, float L, float U, unsigned long long* counts, cudaStream_t s);
 cudaError_t launch_refine(const float* f, float* out, const uint32_t* list, DiagHeader* diag,
                           const RefineParams& rp, cudaStream_t s);
 

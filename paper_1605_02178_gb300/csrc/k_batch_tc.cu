@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(kBRowThreads, 1) k_rows_batch(const BatchWork 
             }
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(&full[s]);
+            if (lane == 0 && !(w.stall == 1 && it == 0)) mbar_arrive(&full[s]);
             load_f(it + NG);
             return true;
         };
@@ -637,6 +637,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cols_batch(const BatchWork w, 
                         ok = false;
                         break;
                     }
+                    if (w.stall == 2 && k == 0) continue;      // (test of the bounded waits)
                     stage_k[s] = k;
                     mbar_expect_tx(&full[s], (unsigned)SP);
                     for (int hh = 0; hh < 2; ++hh) {

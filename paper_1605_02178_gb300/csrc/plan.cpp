@@ -1,5 +1,8 @@
 // Host side of libbfgc: the FP64 coefficient fit (Sec. III), plan management and the
 // C ABI entry points that validate arguments and enqueue the kernels.
+#include <nvtx3/nvToolsExt.h>
+
+#include <cstdio>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -258,9 +261,21 @@ void prof_clear(Profiler& pr) {
     pr.open = -1;
 }
 
-// Record the start of kernel `name` (and thereby the end of the previous one).
+// Record the start of kernel `name` (and thereby the end of the previous one).  Every stage is
+// also an NVTX range on the calling thread ("bfgc <stage>", host-side launch time), whether or
+// not the event profiler is on; without an attached tool the NVTX calls return at once.
 void prof_mark(bf_gc_plan_s* p, const char* name, cudaStream_t s) {
     Profiler& pr = p->prof;
+    if (pr.nvtx_open) {
+        nvtxRangePop();
+        pr.nvtx_open = false;
+    }
+    if (name) {
+        char label[64];
+        std::snprintf(label, sizeof(label), "bfgc %s", name);
+        nvtxRangePushA(label);
+        pr.nvtx_open = true;
+    }
     if (!pr.enabled) return;
     int k = -1;
     if (name) {
@@ -281,6 +296,10 @@ void prof_mark(bf_gc_plan_s* p, const char* name, cudaStream_t s) {
 }
 
 void prof_close(bf_gc_plan_s* p, cudaStream_t s) {
+    if (p->prof.nvtx_open) {
+        nvtxRangePop();
+        p->prof.nvtx_open = false;
+    }
     if (p->prof.enabled && p->prof.open >= 0) prof_mark(p, nullptr, s);
 }
 
@@ -610,6 +629,12 @@ bf_status bf_direct(int H, int W, double sigma_s, double sigma_r, const float* f
     const int R = window_radius(sigma_s);
     if (R > BF_MAX_R) return BF_ERR_UNSUPPORTED;
     return cuda_status(bfgc::launch_direct(f, out, H, W, R, sigma_s, sigma_r, (cudaStream_t)stream));
+}
+
+bf_status bf_check_range(int H, int W, double L, double U, const float* f, unsigned long long* counts,
+                         bf_stream_t stream) {
+    if (H < 1 || W < 1 || !f || !counts || !isfinite(L) || !isfinite(U) || !(L <= U)) return BF_ERR_INVALID_ARG;
+    return cuda_status(bfgc::launch_check_range(f, (size_t)H * W, (float)L, (float)U, counts, (cudaStream_t)stream));
 }
 
 const char* bf_status_string(bf_status s) {

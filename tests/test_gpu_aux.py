@@ -54,3 +54,28 @@ def test_row_pass_kernels_agree_on_repeated_runs():
     assert torch.equal(a, b)
     assert float((a - ref).abs().max()) <= 0.05          # the default kernel sums in another order
     assert np.isfinite(a.cpu().numpy()).all()
+
+
+def test_range_check_counts_planted_pixels():
+    """bf_check_range against numpy's count: pixels outside [L, U] and non-finite ones planted at
+    seeded positions, on an odd-sized image (scalar tail) and through an offset view (no 16-byte
+    alignment)."""
+    from paper_1605_02178_gb300 import bfgc
+    rng = np.random.default_rng(3)
+    H, W = 257, 131
+    f = rng.uniform(0.0, 255.0, (H, W)).astype(np.float32)
+    idx = rng.choice(H * W, 400, replace=False)
+    f.reshape(-1)[idx[:150]] = rng.uniform(256.0, 400.0, 150).astype(np.float32)
+    f.reshape(-1)[idx[150:300]] = rng.uniform(-100.0, -0.5, 150).astype(np.float32)
+    f.reshape(-1)[idx[300:350]] = np.nan
+    f.reshape(-1)[idx[350:400]] = np.inf * np.sign(rng.uniform(-1, 1, 50))
+    fin = np.isfinite(f)
+    want = (int(np.sum(fin & ((f < 0.0) | (f > 255.0)))), int(np.sum(~fin)))
+    t = torch.from_numpy(f).cuda()
+    assert bfgc.bf_check_range(t, 0.0, 255.0) == want == (300, 100)
+    # the same pixels one float off a 16-byte boundary
+    buf = torch.empty(H * W + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = t.reshape(-1)
+    assert bfgc.bf_check_range(buf[1:].view(H, W), 0.0, 255.0) == want
+    # a clean image
+    assert bfgc.bf_check_range(torch.full((5, 3), 7.0, device="cuda"), 0.0, 255.0) == (0, 0)

@@ -99,3 +99,25 @@ def test_persistent_batch_refuses_what_it_cannot_run():
         BT.GCBatch(f, form="fused_tc", precision="bf16", mode="persistent")
     with pytest.raises(BfError):
         BT.GCBatch(SPECS[:2], form="plain", precision="fp32", mode="persistent")
+
+
+@pytest.mark.parametrize("stall,flag", [(1, 4), (2, 8)])
+def test_persistent_batch_wait_runs_out_and_recovers(stall, flag):
+    """The bounded waits of the batched passes: with BF_OPT_STALL on the first plan (1: the row
+    pass's first tile is never handed to the MMA issuer; 2: the column pass's first stage is
+    never loaded) and a 2 ms wait limit, the waits run out, the kernels return and the pass's
+    error flag is set; a following batch without the stall is whole again."""
+    from paper_1605_02178_gb300 import bfgc as B
+    specs = SPECS[:4]
+    fs = _images(specs)
+    bt = BT.GCBatch(specs, form="fused_tc", precision="bf16", mode="persistent")
+    B.bf_gc_plan_set(bt.plans[0].handle, B.BF_OPT_WAIT_US, 2000)
+    B.bf_gc_plan_set(bt.plans[0].handle, B.BF_OPT_STALL, stall)
+    bt.forward(fs)
+    torch.cuda.synchronize()
+    assert bt.diagnostics()["error_flags"] & flag
+    ok = BT.GCBatch(specs, form="fused_tc", precision="bf16", mode="persistent")
+    outs = ok.forward(fs)
+    torch.cuda.synchronize()
+    assert ok.diagnostics()["error_flags"] == 0
+    assert _check(specs, fs, outs, "bf16", BOUND["bf16"] / 2) >= 1
