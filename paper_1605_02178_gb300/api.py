@@ -10,6 +10,10 @@ from . import bfgc as B
 # most 1) does not approximate the filter: the degree N is too low for exp on [-mu, mu],
 # mu = ((U - L) / 2)^2 / sigma_r^2 (about e mu / 2 is needed)
 FIT_DIVERGES = 1.0
+# Beyond this mu (sigma_r below about 37 on [0, 255]) the high-degree fit needs more of the
+# channels' precision than BF16's 8 significant bits keep (measured: 0.67 max-abs against the
+# FP64 oracle at sigma_r = 30, N = 28; within 0.02 at sigma_r >= 40)
+BF16_MU_MAX = 12.0
 
 
 class GCPlan:
@@ -39,10 +43,15 @@ class GCPlan:
         self.form, self.precision, self.poly, self.tile_w = form, precision, poly, tile_w
         self.save_channels = bool(save_channels)
         self._ws = {}
-        fit = self.info["fit_err"]
+        info = self.info
+        fit = info["fit_err"]
         if not fit < FIT_DIVERGES:
             warnings.warn(f"GCPlan: the degree-{N} fit of the range kernel at sigma_r={sigma_r} has worst error "
                           f"{fit:.3g}: the output does not approximate the bilateral filter; raise N",
+                          RuntimeWarning, stacklevel=2)
+        elif precision == "bf16" and info["mu"] > BF16_MU_MAX and info["form"] == B.BF_FORM_FUSED_TC:
+            warnings.warn(f"GCPlan: BF16 channel storage at sigma_r={sigma_r} (mu = {info['mu']:.1f}) can miss the "
+                          f"FP64 result by more than 0.5; precision='fp16' stays within that bound",
                           RuntimeWarning, stacklevel=2)
 
     def __del__(self):

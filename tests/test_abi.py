@@ -205,3 +205,16 @@ def test_plan_warns_when_the_range_fit_diverges():
         warnings.simplefilter("error")
         q = api.GCPlan(64, 64, 3.0, 50.0, 20)
     assert q.info["fit_err"] < 1e-6
+
+
+def test_plan_warns_about_bf16_where_it_misses_the_bound():
+    """sigma_r = 30, N = 28 (the paper's operating point, mu = 18): BF16 storage is flagged, FP16
+    is not; sigma_r = 50 (mu = 6.5) is quiet for BF16."""
+    import warnings
+    from paper_1605_02178_gb300 import api
+    with pytest.warns(RuntimeWarning, match="fp16"):
+        api.GCPlan(64, 64, 3.0, 30.0, 28, form="fused_tc", precision="bf16")
+    with warnings.catch_warnings():
+        warnings.simplefilter("error")
+        api.GCPlan(64, 64, 3.0, 30.0, 28, form="fused_tc", precision="fp16")
+        api.GCPlan(64, 64, 3.0, 50.0, 20, form="fused_tc", precision="bf16")
