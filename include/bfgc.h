@@ -306,7 +306,10 @@ bf_status bf_gc_batch_info(bf_gc_batch_t batch, int *branch_of, int *captures);
  * launches into a CUDA graph (on internal streams, thread-local capture mode); every call
  * then launches that graph on `stream`, so a repeated call costs one graph launch on the
  * host.  Per-image diagnostics are not kept (each branch reuses one diagnostics header);
- * use bf_gc_forward and bf_gc_diagnostics on a plan to inspect one image. */
+ * use bf_gc_forward and bf_gc_diagnostics on a plan to inspect one image.  Persistent mode:
+ * a call with new pointers also rewrites the device work list (tensor maps and pointers of
+ * every image) through a pinned host copy, after synchronising `stream` once so that the
+ * copy is free; repeated calls launch the captured graph only. */
 bf_status bf_gc_batch_forward(bf_gc_batch_t batch, const float *const *d_f, float *const *d_out,
                               void *d_ws, size_t ws_bytes, bf_stream_t stream);
 
