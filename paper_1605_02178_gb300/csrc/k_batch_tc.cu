@@ -806,17 +806,6 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cols_batch(const BatchWork w, 
                 if (m0 >= 1) horner(m0 - 1, z);
             }
             if (!ok) break;
-            // the last tile of image m here: every MMA of image m has completed, so its Toeplitz
-            // slot takes image m + 2's operand (warps 0..3, one lane quarter each)
-            if (cg == 0 && it + 1 < my_tiles && I::item(it + 1) >= s_walk[2]) {
-                const int j2 = I::next_img(w, img_find(w.item0, w.nimg, I::item(it + 1)));
-                if (j2 < w.nimg) {
-                    write_toeplitz(tbase + 128u * (uint32_t)(m & 1), q, lane, w.imgs + j2, ACOLS);
-                    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&tready[m & 1]);
-                }
-            }
             // eq. (10), un-centred; guarded pixels hold their input value.  16-byte stores where
             // the row allows them.  The cheap test (ratio_clear) on every pixel and the quotients
             // stored at once; the few pixels it does not clear take the full decision
@@ -826,20 +815,24 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cols_batch(const BatchWork w, 
             float* orow = *s_out + (size_t)(y < H ? y : 0) * W;
             unsigned odd = 0;
             if (y < H) {
-                float o[16];
+                // four pixels at a time, stored as they are made (few live registers)
+                const bool vec = (W & 3) == 0 && xb + 16 <= W;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    o[j] = __fdividef(s_r * P_[j], Q_[j]) + t_c;
-                    odd |= (unsigned)(xb + j < W && !clear32(u[j], P_[j], Q_[j], Qa[j])) << j;
-                }
-                if ((W & 3) == 0 && xb + 16 <= W) {
+                for (int e = 0; e < 4; ++e) {
+                    float o[4];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        reinterpret_cast<float4*>(orow + xb)[e] = make_float4(o[4 * e], o[4 * e + 1], o[4 * e + 2], o[4 * e + 3]);
-                } else {
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const int j = 4 * e + jj;
+                        o[jj] = __fdividef(s_r * P_[j], Q_[j]) + t_c;
+                        odd |= (unsigned)(xb + j < W && !clear32(u[j], P_[j], Q_[j], Qa[j])) << j;
+                    }
+                    if (vec) {
+                        reinterpret_cast<float4*>(orow + xb)[e] = make_float4(o[0], o[1], o[2], o[3]);
+                    } else {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (xb + j < W) orow[xb + j] = o[j];
+                        for (int jj = 0; jj < 4; ++jj)
+                            if (xb + 4 * e + jj < W) orow[xb + 4 * e + jj] = o[jj];
+                    }
                 }
             }
             if (__any_sync(0xffffffffu, odd != 0)) {
@@ -860,6 +853,18 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cols_batch(const BatchWork w, 
                 for (; redo; redo &= redo - 1) {
                     const int j = __ffs(redo) - 1;
                     orow[xb + j] = __ldg(frow + xb + j);
+                }
+            }
+            // the last tile of image m here: every MMA of image m has completed, so its Toeplitz
+            // slot takes image m + 2's operand (warps 0..3, one lane quarter each; after the
+            // stores, when no pixel state is live)
+            if (cg == 0 && it + 1 < my_tiles && I::item(it + 1) >= s_walk[2]) {
+                const int j2 = I::next_img(w, img_find(w.item0, w.nimg, I::item(it + 1)));
+                if (j2 < w.nimg) {
+                    write_toeplitz(tbase + 128u * (uint32_t)(m & 1), q, lane, w.imgs + j2, ACOLS);
+                    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tready[m & 1]);
                 }
             }
         }
