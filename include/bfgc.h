@@ -300,7 +300,8 @@ bf_status bf_gc_batch_workspace_size(bf_gc_batch_t batch, size_t *bytes);
 bf_status bf_gc_batch_info(bf_gc_batch_t batch, int *branch_of, int *captures);
 
 /* Forward of every image: d_out[i] = B_hat[d_f[i]].  d_f and d_out are HOST arrays of
- * `count` device pointers (16-byte aligned, no input overlapping an output); d_ws is a
+ * `count` device pointers (16-byte aligned, else BF_ERR_INVALID_ARG before any launch; no
+ * input overlapping an output); d_ws is a
  * 256-byte aligned device workspace of at least bf_gc_batch_workspace_size bytes.  The
  * first call, and any call whose pointers differ from the previous one, captures the
  * launches into a CUDA graph (on internal streams, thread-local capture mode); every call

@@ -36,6 +36,7 @@ struct bf_gc_batch_s {
     bool persistent = false;
     int a = 0, grid_rows = 0, grid_cols = 0;
     bool fp16 = false;
+    bool any_pitch = false;                     // an image's rows are not a multiple of 16 bytes
     std::vector<bfgc::BatchImg> imgs;           // host copy of the image table
     std::vector<size_t> y_off;                  // channel buffer of each image in the workspace
     std::vector<int> row0, col0;
@@ -141,8 +142,8 @@ bf_status persistent_forward(bf_gc_batch_s* b, const float* const* d_f, float* c
     if (cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return BF_ERR_CUDA;
     bf_status st = BF_OK;
     if (cudaMemsetAsync(diag, 0, sizeof(DiagHeader), s0) != cudaSuccess ||
-        bfgc::launch_rows_batch(wr, b->a, b->fp16, b->grid_rows, diag, s0) != cudaSuccess ||
-        bfgc::launch_cols_batch(wc, b->a, b->fp16, b->grid_cols, diag, s0) != cudaSuccess)
+        bfgc::launch_rows_batch(wr, b->a, b->fp16, b->any_pitch, b->grid_rows, diag, s0) != cudaSuccess ||
+        bfgc::launch_cols_batch(wc, b->a, b->fp16, b->any_pitch, b->grid_cols, diag, s0) != cudaSuccess)
         st = BF_ERR_CUDA;
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(s0, &graph);
@@ -226,6 +227,7 @@ bf_status bf_gc_batch_create_persistent(int count, const bf_gc_plan_t* plans, bf
     b->branch_of.assign(count, 0);
     b->a = a;
     b->fp16 = plans[0]->precision == BF_PREC_FP16;
+    for (int i = 0; i < count; ++i) b->any_pitch = b->any_pitch || (plans[i]->W & 3) != 0;
     b->imgs.resize(count);
     b->y_off.resize(count);
     std::vector<int> nrow(count), ncol(count);
@@ -292,7 +294,7 @@ bf_status bf_gc_batch_forward(bf_gc_batch_t b, const float* const* d_f, float* c
     if (!d_ws || ((uintptr_t)d_ws & 255) || ws_bytes < b->ws_bytes) return BF_ERR_WORKSPACE;
     const int count = (int)b->plans.size(), nbr = (int)b->members.size();
     for (int i = 0; i < count; ++i)
-        if (!d_f[i] || !d_out[i]) return BF_ERR_INVALID_ARG;
+        if (!d_f[i] || !d_out[i] || ((uintptr_t)d_f[i] & 15) || ((uintptr_t)d_out[i] & 15)) return BF_ERR_INVALID_ARG;
     if (b->persistent) return persistent_forward(b, d_f, d_out, d_ws, (cudaStream_t)stream);
     const bool same = b->exec && b->cap_ws == d_ws && std::equal(b->cap_f.begin(), b->cap_f.end(), d_f) &&
                       std::equal(b->cap_out.begin(), b->cap_out.end(), d_out);

@@ -60,7 +60,11 @@ size_t rows_batch_smem(int a);
 size_t cols_batch_smem(int a);
 int cols_batch_stages(int a);
 
-cudaError_t launch_rows_batch(const BatchWork& w, int a, bool fp16, int grid, DiagHeader* diag, cudaStream_t s);
-cudaError_t launch_cols_batch(const BatchWork& w, int a, bool fp16, int grid, DiagHeader* diag, cudaStream_t s);
+// any_pitch: some image's rows are not a multiple of 16 bytes (W % 4 != 0); such a batch takes
+// the instantiations that also use 8- and 16-byte accesses inside those rows
+cudaError_t launch_rows_batch(const BatchWork& w, int a, bool fp16, bool any_pitch, int grid, DiagHeader* diag,
+                              cudaStream_t s);
+cudaError_t launch_cols_batch(const BatchWork& w, int a, bool fp16, bool any_pitch, int grid, DiagHeader* diag,
+                              cudaStream_t s);
 
 }  // namespace bfgc

@@ -20,7 +20,9 @@
 //     accumulators of image m's last tile (every MMA of image m has completed then), from words
 //     packed on the host (BatchImg::tt), and arrives on tready[slot]; the MMA issuer waits there
 //     before the first MMA of image m + 2.
-// The column pass loads f and stores the output with plain loads and stores (any row pitch);
+// The column pass loads f and stores the output with plain loads and stores (any row pitch).
+// Batches with an image whose rows are not 16 bytes long take instantiations (AP) that also
+// move whole float2s / float4s inside such rows where their alignment allows;
 // the guard of eq. (10) is the FP32 one (no refinement list).  Every wait is bounded.
 #include <cuda.h>
 
@@ -193,7 +195,7 @@ __device__ __forceinline__ int decide32(float P, float Q, float Qa) {
 // Shared layout (1024-byte aligned): S stages of KB K-blocks of 128 rows | NS staging tiles |
 // full[S] | empty[S] | dfull[2] | dempty[2] | staged[NS] | freed[NS] | tready[2] | TMEM slot |
 // abort flag | last tile committed per accumulator buffer [2].
-template <typename T, int A_>
+template <typename T, int A_, bool AP>
 __global__ void __launch_bounds__(kBRowThreads, 1) k_rows_batch(const BatchWork w, DiagHeader* diag, int S, int NS) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
@@ -261,6 +263,16 @@ __global__ void __launch_bounds__(kBRowThreads, 1) k_rows_batch(const BatchWork 
                         const float4 a1 = __ldg(reinterpret_cast<const float4*>(frow + xs + 4));
                         fv[s][0] = a0.x; fv[s][1] = a0.y; fv[s][2] = a0.z; fv[s][3] = a0.w;
                         fv[s][4] = a1.x; fv[s][5] = a1.y; fv[s][6] = a1.z; fv[s][7] = a1.w;
+                    } else if (AP && xs >= 0 && xs + 8 <= W && (((size_t)y * W + xs) & 1) == 0) {
+                        // (rows not 16-byte aligned) inside the row at an even element: float2s
+#pragma unroll
+                        for (int e = 0; e < 8; e += 2) {
+                            const float2 t = __ldg(reinterpret_cast<const float2*>(frow + xs + e));
+                            fv[s][e] = t.x; fv[s][e + 1] = t.y;
+                        }
+                    } else if (AP && xs >= 0 && xs + 8 <= W) {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) fv[s][e] = __ldg(frow + xs + e);
                     } else {
 #pragma unroll
                         for (int e = 0; e < 8; ++e) {
@@ -540,7 +552,7 @@ __global__ void __launch_bounds__(kBRowThreads, 1) k_rows_batch(const BatchWork 
 // per stage [S] | last step committed per accumulator buffer [2] | the epilogue's image
 // parameters and walk.  Pair step k (counted over the CTA's tiles,
 // (C + 1) / 2 per tile of an image with C channels) uses stage k mod S and buffer k mod 2.
-template <typename T, int A_>
+template <typename T, int A_, bool AP>
 __global__ void __launch_bounds__(kCThreads, 1) k_cols_batch(const BatchWork w, DiagHeader* diag, int S) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
@@ -760,6 +772,8 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cols_batch(const BatchWork w, 
                         const float4 v = __ldg(reinterpret_cast<const float4*>(f + (size_t)y * W + xb) + e);
                         u[4 * e] = v.x; u[4 * e + 1] = v.y; u[4 * e + 2] = v.z; u[4 * e + 3] = v.w;
                     }
+                } else if (AP && y < H && xb + 16 <= W) {
+                    ldg_run<16>(f, (size_t)y * W + xb, u);             // any 16-byte phase
                 } else {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) u[j] = (y < H && xb + j < W) ? __ldg(f + (size_t)y * W + xb + j) : 0.0f;
@@ -817,6 +831,7 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cols_batch(const BatchWork w, 
             if (y < H) {
                 // four pixels at a time, stored as they are made (few live registers)
                 const bool vec = (W & 3) == 0 && xb + 16 <= W;
+                const bool vec2 = AP && !vec && xb + 16 <= W && (((size_t)y * W) & 1) == 0;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     float o[4];
@@ -828,6 +843,9 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cols_batch(const BatchWork w, 
                     }
                     if (vec) {
                         reinterpret_cast<float4*>(orow + xb)[e] = make_float4(o[0], o[1], o[2], o[3]);
+                    } else if (vec2) {
+                        reinterpret_cast<float2*>(orow + xb + 4 * e)[0] = make_float2(o[0], o[1]);
+                        reinterpret_cast<float2*>(orow + xb + 4 * e)[1] = make_float2(o[2], o[3]);
                     } else {
 #pragma unroll
                         for (int jj = 0; jj < 4; ++jj)
@@ -927,61 +945,65 @@ size_t cols_batch_smem(int a) {
 
 namespace {
 
-template <typename T, int A>
+template <typename T, int A, bool AP>
 cudaError_t rows_impl(const BatchWork& w, int grid, DiagHeader* diag, cudaStream_t s) {
     int S = 0, NS = 0;
     rows_batch_ring(A, &S, &NS);
     if (S < 2) return cudaErrorInvalidValue;
     const size_t smem = rows_batch_smem(A);
-    auto kern = k_rows_batch<T, A>;
+    auto kern = k_rows_batch<T, A, AP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, kBRowThreads, smem, s>>>(w, diag, S, NS);
     return cudaGetLastError();
 }
 
-template <typename T, int A>
+template <typename T, int A, bool AP>
 cudaError_t cols_impl(const BatchWork& w, int grid, DiagHeader* diag, cudaStream_t s) {
     const int S = cols_batch_stages(A);
     if (S < 2) return cudaErrorInvalidValue;
     const size_t smem = cols_batch_smem(A);
-    auto kern = k_cols_batch<T, A>;
+    auto kern = k_cols_batch<T, A, AP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, kCThreads, smem, s>>>(w, diag, S);
     return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, bool AP>
 cudaError_t rows_a(const BatchWork& w, int a, int grid, DiagHeader* diag, cudaStream_t s) {
     switch (a) {
-    case 1: return rows_impl<T, 1>(w, grid, diag, s);
-    case 2: return rows_impl<T, 2>(w, grid, diag, s);
-    case 3: return rows_impl<T, 3>(w, grid, diag, s);
-    case 4: return rows_impl<T, 4>(w, grid, diag, s);
+    case 1: return rows_impl<T, 1, AP>(w, grid, diag, s);
+    case 2: return rows_impl<T, 2, AP>(w, grid, diag, s);
+    case 3: return rows_impl<T, 3, AP>(w, grid, diag, s);
+    case 4: return rows_impl<T, 4, AP>(w, grid, diag, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-template <typename T>
+template <typename T, bool AP>
 cudaError_t cols_a(const BatchWork& w, int a, int grid, DiagHeader* diag, cudaStream_t s) {
     switch (a) {
-    case 1: return cols_impl<T, 1>(w, grid, diag, s);
-    case 2: return cols_impl<T, 2>(w, grid, diag, s);
-    case 3: return cols_impl<T, 3>(w, grid, diag, s);
-    case 4: return cols_impl<T, 4>(w, grid, diag, s);
+    case 1: return cols_impl<T, 1, AP>(w, grid, diag, s);
+    case 2: return cols_impl<T, 2, AP>(w, grid, diag, s);
+    case 3: return cols_impl<T, 3, AP>(w, grid, diag, s);
+    case 4: return cols_impl<T, 4, AP>(w, grid, diag, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
 }  // namespace
 
-cudaError_t launch_rows_batch(const BatchWork& w, int a, bool fp16, int grid, DiagHeader* diag, cudaStream_t s) {
-    return fp16 ? rows_a<__half>(w, a, grid, diag, s) : rows_a<__nv_bfloat16>(w, a, grid, diag, s);
+cudaError_t launch_rows_batch(const BatchWork& w, int a, bool fp16, bool any_pitch, int grid, DiagHeader* diag,
+                              cudaStream_t s) {
+    if (any_pitch) return fp16 ? rows_a<__half, true>(w, a, grid, diag, s) : rows_a<__nv_bfloat16, true>(w, a, grid, diag, s);
+    return fp16 ? rows_a<__half, false>(w, a, grid, diag, s) : rows_a<__nv_bfloat16, false>(w, a, grid, diag, s);
 }
 
-cudaError_t launch_cols_batch(const BatchWork& w, int a, bool fp16, int grid, DiagHeader* diag, cudaStream_t s) {
-    return fp16 ? cols_a<__half>(w, a, grid, diag, s) : cols_a<__nv_bfloat16>(w, a, grid, diag, s);
+cudaError_t launch_cols_batch(const BatchWork& w, int a, bool fp16, bool any_pitch, int grid, DiagHeader* diag,
+                              cudaStream_t s) {
+    if (any_pitch) return fp16 ? cols_a<__half, true>(w, a, grid, diag, s) : cols_a<__nv_bfloat16, true>(w, a, grid, diag, s);
+    return fp16 ? cols_a<__half, false>(w, a, grid, diag, s) : cols_a<__nv_bfloat16, false>(w, a, grid, diag, s);
 }
 
 }  // namespace bfgc

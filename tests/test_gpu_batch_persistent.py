@@ -82,6 +82,32 @@ def test_persistent_batch_matches_per_image_and_oracle(precision):
     assert bt.info()[1] == 2
 
 
+def test_persistent_aligned_batch():
+    """Every row a multiple of 16 bytes (W % 4 == 0): the batch takes the instantiations with
+    16-byte accesses only (the mixed batches above take those that also handle other pitches)."""
+    specs = [dict(s, W=max(4, s["W"] - s["W"] % 4)) for s in SPECS]
+    assert all(s["W"] % 4 == 0 for s in specs)
+    fs = _images(specs)
+    bt = BT.GCBatch(specs, form="fused_tc", precision="bf16", mode="persistent")
+    outs = bt.forward(fs)
+    torch.cuda.synchronize()
+    assert bt.diagnostics()["error_flags"] == 0
+    assert _check(specs, fs, outs, "bf16", BOUND["bf16"] / 2) >= 4
+
+
+def test_persistent_batch_rejects_misaligned_pointers():
+    """Inputs and outputs must start on 16-byte boundaries (a view one float into a buffer does
+    not): the call fails before any launch."""
+    specs = SPECS[:3]
+    fs = _images(specs)
+    buf = torch.empty(specs[0]["H"] * specs[0]["W"] + 1, device=DEV)
+    shifted = buf[1:].view(specs[0]["H"], specs[0]["W"])
+    shifted.copy_(fs[0])
+    bt = BT.GCBatch(specs, form="fused_tc", precision="bf16", mode="persistent")
+    with pytest.raises(BfError):
+        bt.forward([shifted] + fs[1:])
+
+
 def test_persistent_uneven_batch_against_oracle():
     """48 images of the uneven batch workload (sizes 64..2048, own sigma_s, sigma_r and N)."""
     specs = synth.batch_specs(256, seed=4)[:48]
