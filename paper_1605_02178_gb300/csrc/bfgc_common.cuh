@@ -7,10 +7,10 @@
 
 namespace bfgc {
 
-// A run of L consecutive floats at element i of a 16-byte aligned array, whatever i's phase
-// M = i mod 4: the elements before the first 16-byte boundary as a float and / or a float2,
-// the aligned middle as float4s, the rest as a float2 and / or a float.  Nothing outside the
-// run is touched.  (M is a template argument so that every register index is static.)
+// Load of a run of L consecutive floats at element i of a 16-byte aligned array, whatever i's
+// phase M = i mod 4: the elements before the first 16-byte boundary as a float and / or a
+// float2, the aligned middle as float4s, the rest as a float2 and / or a float.  Nothing
+// outside the run is read.  (M is a template argument so that every register index is static.)
 template <int M, int L>
 __device__ __forceinline__ void ldg_run_m(const float* __restrict__ p, float* v) {
     constexpr int HEAD = (4 - M) & 3;
@@ -25,19 +25,7 @@ __device__ __forceinline__ void ldg_run_m(const float* __restrict__ p, float* v)
     if ((L - HEAD) % 4 >= 2) { const float2 t = __ldg(reinterpret_cast<const float2*>(p + j)); v[j] = t.x; v[j + 1] = t.y; j += 2; }
     if ((L - HEAD) % 2) v[j] = __ldg(p + j);
 }
-template <int M, int L>
-__device__ __forceinline__ void stg_run_m(float* p, const float* v) {
-    constexpr int HEAD = (4 - M) & 3;
-    int j = 0;
-    if (HEAD & 1) { p[0] = v[0]; j = 1; }
-    if (HEAD >= 2) { *reinterpret_cast<float2*>(p + j) = make_float2(v[j], v[j + 1]); j += 2; }
-#pragma unroll
-    for (int k = 0; k < (L - HEAD) / 4; ++k, j += 4)
-        *reinterpret_cast<float4*>(p + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-    if ((L - HEAD) % 4 >= 2) { *reinterpret_cast<float2*>(p + j) = make_float2(v[j], v[j + 1]); j += 2; }
-    if ((L - HEAD) % 2) p[j] = v[j];
-}
-// v[0 .. L) = a[i .. i + L) and a[i .. i + L) = v[0 .. L) for a 16-byte aligned array a
+// v[0 .. L) = a[i .. i + L) for a 16-byte aligned array a
 template <int L>
 __device__ __forceinline__ void ldg_run(const float* __restrict__ a, size_t i, float* v) {
     switch ((unsigned)i & 3u) {
@@ -47,16 +35,6 @@ __device__ __forceinline__ void ldg_run(const float* __restrict__ a, size_t i, f
     default: ldg_run_m<3, L>(a + i, v); break;
     }
 }
-template <int L>
-__device__ __forceinline__ void stg_run(float* a, size_t i, const float* v) {
-    switch ((unsigned)i & 3u) {
-    case 0: stg_run_m<0, L>(a + i, v); break;
-    case 1: stg_run_m<1, L>(a + i, v); break;
-    case 2: stg_run_m<2, L>(a + i, v); break;
-    default: stg_run_m<3, L>(a + i, v); break;
-    }
-}
-
 // Half-sample symmetric extension of index p into [0, n) (period 2n).
 __device__ __forceinline__ int mirror(int p, int n) {
     const int period = 2 * n;
