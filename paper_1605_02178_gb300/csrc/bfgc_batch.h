@@ -51,7 +51,7 @@ struct BatchWork {
     int stall;
 };
 // Chunk sizes of the two passes' work lists (consecutive row-pass / column-pass tiles)
-constexpr int kBatchRowChunk = 4, kBatchColChunk = 1;
+constexpr int kBatchRowChunk = 4, kBatchColChunk = 2;
 
 // Shared-memory ring of the batched row pass at window block count a: stages of KB K-blocks of
 // 128 product rows, staging tiles of 128 rows (the largest product-row count of any image).
