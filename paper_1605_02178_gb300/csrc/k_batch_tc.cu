@@ -820,8 +820,8 @@ __global__ void __launch_bounds__(kCThreads, 1) k_cols_batch(const BatchWork w, 
                 if (m0 >= 1) horner(m0 - 1, z);
             }
             if (!ok) break;
-            // eq. (10), un-centred; guarded pixels hold their input value.  16-byte stores where
-            // the row allows them.  The cheap test (ratio_clear) on every pixel and the quotients
+            // eq. (10), un-centred; guarded pixels hold their input value.  16-byte (else 8-byte)
+            // stores where the row allows them.  The cheap test (ratio_clear) on every pixel and the quotients
             // stored at once; the few pixels it does not clear take the full decision
             // (ratio_decision) afterwards and are rewritten.  (Rows past the image: nothing
             // stored, no pixel odd; the warp vote is taken by all lanes.)
