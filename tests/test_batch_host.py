@@ -77,6 +77,11 @@ def test_batch_forward_rejects_bad_workspace_before_any_cuda_call():
         nul = (ctypes.c_void_p * 2)(16, None)
         st = B.lib().bf_gc_batch_forward(h, nul, arr, ctypes.c_void_p(256), 1 << 40, None)
         assert st == B.BF_ERR_INVALID_ARG
+        # inputs and outputs start on 16-byte boundaries
+        for bad_f, bad_o in (((16, 36), (16, 32)), ((16, 32), (24, 32))):
+            pf, po = (ctypes.c_void_p * 2)(*bad_f), (ctypes.c_void_p * 2)(*bad_o)
+            st = B.lib().bf_gc_batch_forward(h, pf, po, ctypes.c_void_p(256), 1 << 40, None)
+            assert st == B.BF_ERR_INVALID_ARG
     finally:
         B.bf_gc_batch_destroy(h)
 
